@@ -1,0 +1,272 @@
+/*
+ * FP64 reference Range-Doppler compressor -- TEST INFRASTRUCTURE ONLY.
+ *
+ * This file is the oracle that the CUDA path is checked against.  Only the
+ * test-suite, the smoke check and the benchmark's CPU-baseline leg load it;
+ * the product library never links, loads or calls it, and it shares no code,
+ * header, table or constant with the CUDA sources.
+ *
+ * It is deliberately plain and slow: every step is written out as the
+ * paper states it, in double precision, with no blocking, fusion or
+ * reordering beyond that statement, so that it can be checked by eye.
+ *
+ *   Range compression (Sec. IV-A, step 1; Sec. II-B):
+ *       per azimuth line x:  y = IFFT( FFT(x) . H_r )
+ *   Corner turn (Sec. IV-A step 2 / Sec. IV-B: the transpose that turns the
+ *       azimuth columns into rows):  out[c][r] = in[r][c]
+ *   Azimuth compression (Sec. IV-A, step 4, in the form used here: a full
+ *       FFT -> x H_a -> IFFT per range bin after the corner turn).
+ *   IFFT (Sec. II-C):  IFFT(X) = (1/N) * sum_k X[k] exp(+2 pi i n k / N);
+ *       the paper computes it as conj(FFT(conj X))/N, which is the same value.
+ *   Matched filter (Sec. II-B, "pre-computed matched filter"): the reference
+ *       chirp c, centred on time index 0 with circular wrap, gives
+ *       H = conj(FFT_N(c)), unnormalised.  Correlating with it puts the
+ *       compressed peak of a target exactly at the target's position.
+ *
+ * The FFT is a textbook iterative radix-2 decimation-in-time transform.  Each
+ * twiddle factor exp(sign * 2 pi i j / len) is evaluated directly with cos()
+ * and sin() for its own index j -- never by a recurrence -- so its error does
+ * not grow with the transform length.
+ *
+ * Data layout: complex numbers are pairs of doubles (re, im), i.e. the
+ * memory layout of C99 double complex and of numpy.complex128.  Matrices are
+ * row-major.  All entry points return 0 on success and a negative value on a
+ * bad argument; none of them allocates memory visible to the caller.
+ *
+ * Planted mistakes: when compiled with -DORACLE_PLANT=<k> (k >= 1) one
+ * deliberate error is introduced (see the ORACLE_PLANT blocks).  The test
+ * suite builds each variant in a temporary directory and checks that its
+ * pins fail; the default build has ORACLE_PLANT = 0 and no planted error.
+ */
+#include <complex.h>
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef ORACLE_PLANT
+#define ORACLE_PLANT 0
+#endif
+
+typedef double complex cplx;
+
+static const double kTwoPi = 6.283185307179586476925286766559;
+
+static int is_pow2(int64_t n) { return n >= 1 && (n & (n - 1)) == 0; }
+
+/* ------------------------------------------------------------------------ */
+/* Discrete Fourier transform (definition:  X[k] = sum_n x[n] e^{sign 2 pi i n k / N}). */
+/* ------------------------------------------------------------------------ */
+
+/* In-place unnormalised radix-2 FFT of length n (a power of two).
+ * sign = -1: forward transform; sign = +1: inverse kernel (no 1/N). */
+int oracle_fft(int64_t n, cplx *x, int sign)
+{
+    if (!is_pow2(n) || (sign != 1 && sign != -1) || (n > 0 && !x))
+        return -1;
+#if ORACLE_PLANT == 1
+    sign = -sign; /* planted: wrong exponent sign */
+#endif
+    /* bit-reversal permutation */
+    for (int64_t i = 1, j = 0; i < n; ++i) {
+        int64_t bit = n >> 1;
+        for (; j & bit; bit >>= 1)
+            j ^= bit;
+        j ^= bit;
+        if (i < j) {
+            cplx t = x[i];
+            x[i] = x[j];
+            x[j] = t;
+        }
+    }
+    /* butterflies, span len = 2, 4, ..., n */
+    for (int64_t len = 2; len <= n; len <<= 1) {
+        int64_t half = len >> 1;
+        for (int64_t j = 0; j < half; ++j) {
+            double ang = (double)sign * kTwoPi * (double)j / (double)len;
+            cplx w = cos(ang) + I * sin(ang);
+#if ORACLE_PLANT == 2
+            if (j == 1) w = conj(w); /* planted: one wrong twiddle */
+#endif
+            for (int64_t i = 0; i < n; i += len) {
+                cplx u = x[i + j];
+                cplx v = x[i + j + half] * w;
+                x[i + j] = u + v;
+                x[i + j + half] = u - v;
+            }
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Matched filter (Sec. II-B step 3, Sec. IV-A steps 1 and 4).               */
+/* ------------------------------------------------------------------------ */
+
+/* H[k] = conj( sum_m c(m) e^{-2 pi i m k / n} ) where the reference chirp
+ * sample chirp[j] belongs to time index m = j - n_chirp/2 (the chirp is
+ * centred on index 0) and sits at position m mod n of a length-n line. */
+int oracle_matched_filter(int64_t n, int64_t n_chirp, const cplx *chirp, cplx *H)
+{
+    if (!is_pow2(n) || n_chirp < 1 || n_chirp > n || !chirp || !H)
+        return -1;
+    memset(H, 0, sizeof(cplx) * (size_t)n);
+    for (int64_t j = 0; j < n_chirp; ++j) {
+        int64_t m = j - n_chirp / 2;
+#if ORACLE_PLANT == 3
+        m = j; /* planted: chirp not centred on index 0 */
+#endif
+        int64_t pos = ((m % n) + n) % n;
+        H[pos] += chirp[j];
+    }
+    if (oracle_fft(n, H, -1))
+        return -1;
+    for (int64_t k = 0; k < n; ++k) {
+#if ORACLE_PLANT == 4
+        continue; /* planted: filter not conjugated */
+#endif
+        H[k] = conj(H[k]);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Fused line compression: y = IFFT(FFT(x) . H), Sec. II-B steps 1-5.        */
+/* ------------------------------------------------------------------------ */
+
+/* One line of length n, in place. */
+int oracle_compress_line(int64_t n, cplx *x, const cplx *H)
+{
+    if (!is_pow2(n) || !x || !H)
+        return -1;
+    if (oracle_fft(n, x, -1))
+        return -1;
+    for (int64_t k = 0; k < n; ++k)
+        x[k] *= H[k];
+    if (oracle_fft(n, x, +1))
+        return -1;
+    double inv_n = 1.0 / (double)n;
+#if ORACLE_PLANT == 5
+    inv_n = 1.0; /* planted: 1/N of the IFFT dropped */
+#endif
+    for (int64_t k = 0; k < n; ++k)
+        x[k] *= inv_n;
+    return 0;
+}
+
+typedef struct {
+    int64_t n_lines, n;
+    cplx *data;
+    const cplx *H;
+    int tid, nthreads, status;
+} line_job;
+
+static void *line_worker(void *arg)
+{
+    line_job *job = (line_job *)arg;
+    for (int64_t l = job->tid; l < job->n_lines; l += job->nthreads)
+        if (oracle_compress_line(job->n, job->data + l * job->n, job->H))
+            job->status = -1;
+    return NULL;
+}
+
+/* Every one of n_lines contiguous lines of length n, in place.  Line l is
+ * handled by worker (l mod nthreads); each line's result is independent of
+ * the thread count. */
+int oracle_compress_lines(int64_t n_lines, int64_t n, cplx *data, const cplx *H, int nthreads)
+{
+    if (n_lines < 0 || !is_pow2(n) || (n_lines > 0 && !data) || !H)
+        return -1;
+    if (nthreads < 1)
+        nthreads = 1;
+    if (nthreads > 256)
+        nthreads = 256;
+    if ((int64_t)nthreads > n_lines)
+        nthreads = n_lines > 0 ? (int)n_lines : 1;
+    line_job jobs[256];
+    pthread_t th[256];
+    for (int t = 0; t < nthreads; ++t) {
+        jobs[t] = (line_job){n_lines, n, data, H, t, nthreads, 0};
+    }
+    int spawned = 0;
+    for (int t = 1; t < nthreads; ++t) {
+        if (pthread_create(&th[t], NULL, line_worker, &jobs[t]) != 0)
+            break;
+        spawned = t;
+    }
+    /* whatever could not be spawned runs here */
+    for (int t = spawned + 1; t < nthreads; ++t)
+        line_worker(&jobs[t]);
+    line_worker(&jobs[0]);
+    for (int t = 1; t <= spawned; ++t)
+        pthread_join(th[t], NULL);
+    for (int t = 0; t < nthreads; ++t)
+        if (jobs[t].status)
+            return -1;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Corner turn (Sec. IV-A step 2, Sec. IV-B):  out[c][r] = in[r][c].          */
+/* ------------------------------------------------------------------------ */
+
+int oracle_corner_turn(int64_t rows, int64_t cols, const cplx *in, cplx *out)
+{
+    if (rows < 0 || cols < 0 || ((rows * cols) > 0 && (!in || !out)))
+        return -1;
+    for (int64_t r = 0; r < rows; ++r)
+        for (int64_t c = 0; c < cols; ++c) {
+#if ORACLE_PLANT == 6
+            if (r == 1 && c == 0) { out[c * rows + r] = in[0]; continue; } /* planted: wrong index */
+#endif
+            out[c * rows + r] = in[r * cols + c];
+        }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Range-Doppler compression of one scene (Sec. IV-A steps 1, 2, 4).         */
+/* ------------------------------------------------------------------------ */
+
+/* raw:   n_az x n_range echo (azimuth-major rows), read only.
+ * Hr:    range filter spectrum, n_range values.
+ * Ha:    azimuth filter spectrum, l_az values.
+ * image: n_range x n_az output (range-bin-major rows).
+ * l_az:  azimuth transform length (a power of two >= n_az).  When n_az is
+ *        smaller the azimuth lines are zero-padded to l_az before the FFT and
+ *        cropped back to n_az after the IFFT (circular correlation at length
+ *        l_az).  With l_az == n_az this is the plain three-step algorithm. */
+int oracle_rda(int64_t n_az, int64_t n_range, int64_t l_az, const cplx *raw, const cplx *Hr,
+               const cplx *Ha, cplx *image, int nthreads)
+{
+    if (n_az < 1 || !is_pow2(n_range) || !is_pow2(l_az) || l_az < n_az || !raw || !Hr || !Ha ||
+        !image)
+        return -1;
+    cplx *work = (cplx *)malloc(sizeof(cplx) * (size_t)(n_az * n_range));
+    cplx *az = (cplx *)calloc((size_t)(n_range * l_az), sizeof(cplx));
+    if (!work || !az) {
+        free(work);
+        free(az);
+        return -1;
+    }
+    int st = 0;
+    /* 1. range compression of every azimuth line */
+    memcpy(work, raw, sizeof(cplx) * (size_t)(n_az * n_range));
+    st |= oracle_compress_lines(n_az, n_range, work, Hr, nthreads);
+    /* 2. corner turn into zero-padded azimuth lines */
+    for (int64_t a = 0; a < n_az; ++a)
+        for (int64_t r = 0; r < n_range; ++r)
+            az[r * l_az + a] = work[a * n_range + r];
+    /* 3. azimuth compression of every range bin */
+    st |= oracle_compress_lines(n_range, l_az, az, Ha, nthreads);
+    /* 4. crop */
+    for (int64_t r = 0; r < n_range; ++r)
+        memcpy(image + r * n_az, az + r * l_az, sizeof(cplx) * (size_t)n_az);
+    free(work);
+    free(az);
+    return st ? -1 : 0;
+}
+
+/* Which planted mistake this build carries (0 = none). */
+int oracle_planted(void) { return ORACLE_PLANT; }
