@@ -1,0 +1,192 @@
+"""Python binding of libsar, the GB300 (sm_103a) kernel-fused SAR Range-Doppler
+compression library.
+
+This module only marshals arguments: every step of the compression runs in
+the CUDA kernels of ``libsar.so`` (built in-tree from ``csrc/`` by
+``build.py``).  The function names are those of the C-ABI in
+``include/sar.h``.  If the library is missing, importing this package raises
+ImportError; there is no fallback of any kind.
+
+Tensors are torch tensors of dtype complex64 on the current CUDA device
+(contiguous); streams default to torch's current stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsar.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libsar.so is not built ({LIB_PATH}); run paper_2604_03585_gb300/build.py "
+                      "or __graft_entry__.build() first")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+SAR_OK, SAR_ERR_INVALID_ARG, SAR_ERR_UNSUPPORTED, SAR_ERR_OUT_OF_MEMORY, SAR_ERR_CUDA, SAR_ERR_TIMEOUT = range(6)
+SAR_PREC_FP32 = 0
+
+STATUS_NAMES = {0: "SAR_OK", 1: "SAR_ERR_INVALID_ARG", 2: "SAR_ERR_UNSUPPORTED",
+                3: "SAR_ERR_OUT_OF_MEMORY", 4: "SAR_ERR_CUDA", 5: "SAR_ERR_TIMEOUT"}
+
+# every entry point declared in include/sar.h
+EXPORTS = ("sar_plan_create", "sar_plan_destroy", "sar_range_compress", "sar_corner_turn",
+           "sar_azimuth_compress", "sar_rda_process", "sar_range_compress_oop", "sar_rda_process_oop",
+           "sar_rda_process_host", "sar_make_lfm_spectrum",
+           "sar_fft_lines", "sar_transpose", "sar_sync", "sar_last_error", "sar_version")
+
+
+class sar_filters(ctypes.Structure):
+    _fields_ = [("range_spectrum", ctypes.c_void_p), ("az_spectrum", ctypes.c_void_p),
+                ("precision", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+_i64, _vp, _int, _dbl = ctypes.c_int64, ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+_SIGS = {
+    "sar_plan_create": [_i64, _i64, ctypes.POINTER(sar_filters), ctypes.POINTER(_vp)],
+    "sar_plan_destroy": [_vp],
+    "sar_range_compress": [_vp, _vp, _vp],
+    "sar_corner_turn": [_vp, _vp, _vp, _vp],
+    "sar_azimuth_compress": [_vp, _vp, _vp],
+    "sar_rda_process": [_vp, _vp, _vp, _vp],
+    "sar_range_compress_oop": [_vp, _vp, _vp, _vp],
+    "sar_rda_process_oop": [_vp, _vp, _vp, _vp, _vp],
+    "sar_rda_process_host": [_vp, _vp, _vp, _vp],
+    "sar_make_lfm_spectrum": [_i64, _i64, _dbl, _vp, _vp],
+    "sar_fft_lines": [_i64, _i64, _vp, _vp, _int, _vp],
+    "sar_transpose": [_i64, _i64, _vp, _vp, _vp],
+    "sar_sync": [_vp],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_int
+_lib.sar_last_error.restype = ctypes.c_char_p
+_lib.sar_version.restype = ctypes.c_char_p
+
+
+class SarError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+def _check(st: int) -> None:
+    if st != SAR_OK:
+        raise SarError(st, _lib.sar_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(x):
+    """Device (or host) address of a tensor / numpy array / raw int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def library() -> ctypes.CDLL:
+    return _lib
+
+
+def sar_version() -> str:
+    return _lib.sar_version().decode()
+
+
+def sar_last_error() -> str:
+    return _lib.sar_last_error().decode()
+
+
+class Plan:
+    """An opaque sar_plan handle (destroyed with the object or explicitly)."""
+
+    def __init__(self, handle: int, n_range: int, n_az: int):
+        self.handle = handle
+        self.n_range = n_range
+        self.n_az = n_az
+
+    def destroy(self) -> None:
+        if self.handle:
+            _check(_lib.sar_plan_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def sar_plan_create(n_range: int, n_az: int, range_spectrum, az_spectrum, precision: int = SAR_PREC_FP32,
+                    flags: int = 0) -> Plan:
+    f = sar_filters(_ptr(range_spectrum), _ptr(az_spectrum), precision, flags)
+    h = _vp()
+    _check(_lib.sar_plan_create(n_range, n_az, ctypes.byref(f), ctypes.byref(h)))
+    return Plan(h.value, n_range, n_az)
+
+
+def sar_plan_destroy(plan: Plan) -> None:
+    plan.destroy()
+
+
+def _h(plan):
+    return plan.handle if isinstance(plan, Plan) else plan
+
+
+def sar_range_compress(plan, data, stream=None) -> None:
+    _check(_lib.sar_range_compress(_h(plan), _ptr(data), _stream(stream)))
+
+
+def sar_corner_turn(plan, inp, out, stream=None) -> None:
+    _check(_lib.sar_corner_turn(_h(plan), _ptr(inp), _ptr(out), _stream(stream)))
+
+
+def sar_azimuth_compress(plan, data, stream=None) -> None:
+    _check(_lib.sar_azimuth_compress(_h(plan), _ptr(data), _stream(stream)))
+
+
+def sar_rda_process(plan, raw, image, stream=None) -> None:
+    _check(_lib.sar_rda_process(_h(plan), _ptr(raw), _ptr(image), _stream(stream)))
+
+
+def sar_range_compress_oop(plan, inp, out, stream=None) -> None:
+    _check(_lib.sar_range_compress_oop(_h(plan), _ptr(inp), _ptr(out), _stream(stream)))
+
+
+def sar_rda_process_oop(plan, raw, work, image, stream=None) -> None:
+    _check(_lib.sar_rda_process_oop(_h(plan), _ptr(raw), _ptr(work), _ptr(image), _stream(stream)))
+
+
+def sar_rda_process_host(plan, raw_host, image_host, stream=None) -> None:
+    _check(_lib.sar_rda_process_host(_h(plan), _ptr(raw_host), _ptr(image_host), _stream(stream)))
+
+
+def sar_make_lfm_spectrum(n: int, n_chirp: int, tbp: float, out, stream=None) -> None:
+    _check(_lib.sar_make_lfm_spectrum(n, n_chirp, float(tbp), _ptr(out), _stream(stream)))
+
+
+def sar_fft_lines(n: int, n_lines: int, inp, out, inverse: bool = False, stream=None) -> None:
+    _check(_lib.sar_fft_lines(n, n_lines, _ptr(inp), _ptr(out), 1 if inverse else 0, _stream(stream)))
+
+
+def sar_transpose(rows: int, cols: int, inp, out, stream=None) -> None:
+    _check(_lib.sar_transpose(rows, cols, _ptr(inp), _ptr(out), _stream(stream)))
+
+
+def sar_sync(stream=None) -> None:
+    _check(_lib.sar_sync(_stream(stream)))

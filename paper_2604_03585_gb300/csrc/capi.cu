@@ -1,0 +1,390 @@
+// C-ABI of libsar: plan lifecycle, argument validation and the entry points
+// declared in include/sar.h.  All compute runs in this library's kernels;
+// there is no host or library fallback.
+#include <mutex>
+#include <new>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+#include <string>
+#include <vector>
+
+#include "../../include/sar.h"
+#include "registry.h"
+#include "tables.h"
+
+using sar::SchedDesc;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+sar_status fail(sar_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+sar_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(SAR_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define SAR_CUDA(call, what)                          \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+bool is_pow2(int64_t n) { return n >= 1 && (n & (n - 1)) == 0; }
+
+sar_status check_length(int64_t n, const char *what) {
+    if (n < 1) return fail(SAR_ERR_INVALID_ARG, "%s = %lld must be >= 1", what, (long long)n);
+    if (!is_pow2(n) || n < 256 || n > 16384)
+        return fail(SAR_ERR_UNSUPPORTED, "%s = %lld: supported lengths are powers of two in [256, 16384]", what,
+                    (long long)n);
+    return SAR_OK;
+}
+
+// A compute pointer must be non-null, 16-byte aligned and device-accessible
+// memory of the current device (a host pointer handed to a kernel would
+// fault the GPU, so it is refused here).
+sar_status check_device_ptr(const void *p, const char *what) {
+    if (!p) return fail(SAR_ERR_INVALID_ARG, "%s is NULL", what);
+    if (((uintptr_t)p) & 15u) return fail(SAR_ERR_INVALID_ARG, "%s is not 16-byte aligned", what);
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SAR_ERR_INVALID_ARG, "%s: not a CUDA pointer (%s)", what, cudaGetErrorName(e));
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return fail(SAR_ERR_INVALID_ARG, "%s is not device memory", what);
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (a.device != dev) return fail(SAR_ERR_INVALID_ARG, "%s lives on device %d, current device is %d", what,
+                                     a.device, dev);
+    return SAR_OK;
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct LinePlan {
+    const SchedDesc *sched = nullptr;
+    float2 *filt = nullptr;  // n complex, register order, 1/N folded in
+    float2 *tw = nullptr;    // twiddle tables
+};
+
+// Per-device cache of twiddle tables for the stand-alone FFT entry points.
+struct TwiddleCache {
+    std::mutex mu;
+    std::vector<std::pair<const SchedDesc *, float2 *>> tables[64];
+};
+TwiddleCache g_tw;
+
+sar_status cached_twiddles(const SchedDesc *d, float2 **out) {
+    int dev = 0;
+    SAR_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(SAR_ERR_UNSUPPORTED, "device index %d", dev);
+    std::lock_guard<std::mutex> lk(g_tw.mu);
+    for (auto &pr : g_tw.tables[dev])
+        if (pr.first == d) {
+            *out = pr.second;
+            return SAR_OK;
+        }
+    float2 *tw = nullptr;
+    cudaError_t e = cudaMalloc(&tw, sizeof(float2) * (size_t)d->tw_elems);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SAR_ERR_OUT_OF_MEMORY, "twiddle table allocation failed");
+    }
+    cudaStream_t s;
+    SAR_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "cudaStreamCreate");
+    e = sar::build_twiddles(*d, tw, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    if (e != cudaSuccess) {
+        cudaFree(tw);
+        return cuda_fail(e, "twiddle table");
+    }
+    SAR_CUDA(d->prepare(), "cudaFuncSetAttribute");
+    g_tw.tables[dev].push_back({d, tw});
+    *out = tw;
+    return SAR_OK;
+}
+
+bool fault_inject_alloc() {
+    const char *v = getenv("SAR_FAULT_INJECT_ALLOC");
+    return v && v[0] == '1';
+}
+
+}  // namespace
+
+struct sar_plan_s {
+    int64_t n_range = 0, n_az = 0;
+    int device = 0;
+    LinePlan range, az;
+    void *block = nullptr;  // one device allocation holding every table
+    std::mutex host_mu;
+    void *stage_raw = nullptr, *stage_img = nullptr;  // lazily, for the host-buffer entry point
+};
+
+extern "C" {
+
+const char *sar_last_error(void) { return g_last_error.c_str(); }
+
+const char *sar_version(void) { return "sar-gb300 0.1 (sm_103a)"; }
+
+sar_status sar_plan_create(int64_t n_range, int64_t n_az, const sar_filters *filters, sar_plan *out) {
+    if (!out) return fail(SAR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!filters) return fail(SAR_ERR_INVALID_ARG, "filters is NULL");
+    sar_status st;
+    if ((st = check_length(n_range, "n_range")) != SAR_OK) return st;
+    if ((st = check_length(n_az, "n_az")) != SAR_OK) return st;
+    if (filters->flags != 0) return fail(SAR_ERR_INVALID_ARG, "filters->flags must be 0");
+    if (filters->precision != SAR_PREC_FP32)
+        return fail(SAR_ERR_UNSUPPORTED, "precision %d is not available", (int)filters->precision);
+    if ((st = check_device_ptr(filters->range_spectrum, "filters->range_spectrum")) != SAR_OK) return st;
+    if ((st = check_device_ptr(filters->az_spectrum, "filters->az_spectrum")) != SAR_OK) return st;
+
+    const SchedDesc *dr = sar::default_schedule((int)n_range);
+    const SchedDesc *da = sar::default_schedule((int)n_az);
+    if (!dr || !da) return fail(SAR_ERR_UNSUPPORTED, "no compiled schedule for this size");
+
+    sar_plan p = new (std::nothrow) sar_plan_s;
+    if (!p) return fail(SAR_ERR_OUT_OF_MEMORY, "host allocation failed");
+    p->n_range = n_range;
+    p->n_az = n_az;
+    cudaGetDevice(&p->device);
+    p->range.sched = dr;
+    p->az.sched = da;
+
+    // one block: filt_r | tw_r | filt_a | tw_a | idx (int32, max n)
+    const size_t o_fr = 0;
+    const size_t o_tr = o_fr + align_up(sizeof(float2) * (size_t)n_range);
+    const size_t o_fa = o_tr + align_up(sizeof(float2) * (size_t)dr->tw_elems);
+    const size_t o_ta = o_fa + align_up(sizeof(float2) * (size_t)n_az);
+    const size_t o_ix = o_ta + align_up(sizeof(float2) * (size_t)da->tw_elems);
+    const size_t total = o_ix + align_up(sizeof(int32_t) * (size_t)(n_range > n_az ? n_range : n_az));
+    cudaError_t e = fault_inject_alloc() ? cudaErrorMemoryAllocation : cudaMalloc(&p->block, total);
+    if (e != cudaSuccess) {
+        if (e != cudaErrorMemoryAllocation) cudaGetLastError();
+        else cudaGetLastError();
+        delete p;
+        return fail(SAR_ERR_OUT_OF_MEMORY, "plan allocation of %zu bytes failed", total);
+    }
+    char *b = (char *)p->block;
+    p->range.filt = (float2 *)(b + o_fr);
+    p->range.tw = (float2 *)(b + o_tr);
+    p->az.filt = (float2 *)(b + o_fa);
+    p->az.tw = (float2 *)(b + o_ta);
+    int32_t *idx_dev = (int32_t *)(b + o_ix);
+
+    cudaStream_t s = nullptr;
+    std::vector<int32_t> idx;
+    auto cleanup_fail = [&](cudaError_t err, const char *what) {
+        if (s) cudaStreamDestroy(s);
+        cudaFree(p->block);
+        delete p;
+        return cuda_fail(err, what);
+    };
+    if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess)
+        return cleanup_fail(e, "cudaStreamCreate");
+    // the caller's spectra were produced on the legacy stream or another one:
+    // wait for the device once before reading them
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cleanup_fail(e, "cudaDeviceSynchronize");
+    const struct {
+        LinePlan *lp;
+        const void *H;
+    } dims[2] = {{&p->range, filters->range_spectrum}, {&p->az, filters->az_spectrum}};
+    for (auto &dm : dims) {
+        const SchedDesc &d = *dm.lp->sched;
+        if ((e = d.prepare()) != cudaSuccess) return cleanup_fail(e, "cudaFuncSetAttribute");
+        if ((e = sar::build_twiddles(d, dm.lp->tw, s)) != cudaSuccess) return cleanup_fail(e, "twiddle tables");
+        idx.assign(d.n, 0);
+        sar::filter_slot_to_k(d, idx.data());
+        if ((e = cudaMemcpyAsync(idx_dev, idx.data(), sizeof(int32_t) * d.n, cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess)
+            return cleanup_fail(e, "filter index copy");
+        if ((e = sar::build_filter(d, (const float2 *)dm.H, dm.lp->filt, idx_dev, s)) != cudaSuccess)
+            return cleanup_fail(e, "filter permutation");
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cleanup_fail(e, "plan tables");
+    }
+    cudaStreamDestroy(s);
+    *out = p;
+    return SAR_OK;
+}
+
+sar_status sar_plan_destroy(sar_plan p) {
+    if (!p) return SAR_OK;
+    cudaFree(p->block);
+    if (p->stage_raw) cudaFree(p->stage_raw);
+    if (p->stage_img) cudaFree(p->stage_img);
+    delete p;
+    return SAR_OK;
+}
+
+static sar_status run_fused(const LinePlan &lp, int64_t n_lines, const void *in, void *out, cudaStream_t s,
+                            const char *what) {
+    const SchedDesc &d = *lp.sched;
+    cudaError_t e = d.fused((const float2 *)in, (float2 *)out, n_lines, d.n, d.n, lp.filt, lp.tw, s);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return SAR_OK;
+}
+
+sar_status sar_range_compress(sar_plan p, void *data, sar_stream stream) {
+    if (!p) return fail(SAR_ERR_INVALID_ARG, "plan is NULL");
+    sar_status st = check_device_ptr(data, "data");
+    if (st != SAR_OK) return st;
+    return run_fused(p->range, p->n_az, data, data, (cudaStream_t)stream, "range compression launch");
+}
+
+sar_status sar_azimuth_compress(sar_plan p, void *data, sar_stream stream) {
+    if (!p) return fail(SAR_ERR_INVALID_ARG, "plan is NULL");
+    sar_status st = check_device_ptr(data, "data");
+    if (st != SAR_OK) return st;
+    return run_fused(p->az, p->n_range, data, data, (cudaStream_t)stream, "azimuth compression launch");
+}
+
+static bool overlaps(const void *a, const void *b, size_t bytes) {
+    const char *x = (const char *)a, *y = (const char *)b;
+    return x < y + bytes && y < x + bytes;
+}
+
+sar_status sar_corner_turn(sar_plan p, const void *in, void *out, sar_stream stream) {
+    if (!p) return fail(SAR_ERR_INVALID_ARG, "plan is NULL");
+    sar_status st;
+    if ((st = check_device_ptr(in, "in")) != SAR_OK) return st;
+    if ((st = check_device_ptr(out, "out")) != SAR_OK) return st;
+    if (overlaps(in, out, sizeof(float2) * (size_t)(p->n_az * p->n_range)))
+        return fail(SAR_ERR_INVALID_ARG, "in and out overlap");
+    cudaError_t e = sar::launch_transpose((const float2 *)in, (float2 *)out, p->n_az, p->n_range, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "corner turn launch");
+    return SAR_OK;
+}
+
+sar_status sar_rda_process(sar_plan p, void *raw, void *image, sar_stream stream) {
+    if (!p) return fail(SAR_ERR_INVALID_ARG, "plan is NULL");
+    sar_status st;
+    if ((st = check_device_ptr(raw, "raw")) != SAR_OK) return st;
+    if ((st = check_device_ptr(image, "image")) != SAR_OK) return st;
+    if (overlaps(raw, image, sizeof(float2) * (size_t)(p->n_az * p->n_range)))
+        return fail(SAR_ERR_INVALID_ARG, "raw and image overlap");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = run_fused(p->range, p->n_az, raw, raw, s, "range compression launch")) != SAR_OK) return st;
+    cudaError_t e = sar::launch_transpose((const float2 *)raw, (float2 *)image, p->n_az, p->n_range, s);
+    if (e != cudaSuccess) return cuda_fail(e, "corner turn launch");
+    return run_fused(p->az, p->n_range, image, image, s, "azimuth compression launch");
+}
+
+sar_status sar_range_compress_oop(sar_plan p, const void *in, void *out, sar_stream stream) {
+    if (!p) return fail(SAR_ERR_INVALID_ARG, "plan is NULL");
+    sar_status st;
+    if ((st = check_device_ptr(in, "in")) != SAR_OK) return st;
+    if ((st = check_device_ptr(out, "out")) != SAR_OK) return st;
+    if (in != out && overlaps(in, out, sizeof(float2) * (size_t)(p->n_az * p->n_range)))
+        return fail(SAR_ERR_INVALID_ARG, "in and out partially overlap");
+    return run_fused(p->range, p->n_az, in, out, (cudaStream_t)stream, "range compression launch");
+}
+
+sar_status sar_rda_process_oop(sar_plan p, const void *raw, void *work, void *image, sar_stream stream) {
+    if (!p) return fail(SAR_ERR_INVALID_ARG, "plan is NULL");
+    sar_status st;
+    if ((st = check_device_ptr(raw, "raw")) != SAR_OK) return st;
+    if ((st = check_device_ptr(work, "work")) != SAR_OK) return st;
+    if ((st = check_device_ptr(image, "image")) != SAR_OK) return st;
+    const size_t bytes = sizeof(float2) * (size_t)(p->n_az * p->n_range);
+    if (overlaps(raw, work, bytes) || overlaps(raw, image, bytes) || overlaps(work, image, bytes))
+        return fail(SAR_ERR_INVALID_ARG, "raw, work and image must not overlap");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = run_fused(p->range, p->n_az, raw, work, s, "range compression launch")) != SAR_OK) return st;
+    cudaError_t e = sar::launch_transpose((const float2 *)work, (float2 *)image, p->n_az, p->n_range, s);
+    if (e != cudaSuccess) return cuda_fail(e, "corner turn launch");
+    return run_fused(p->az, p->n_range, image, image, s, "azimuth compression launch");
+}
+
+sar_status sar_rda_process_host(sar_plan p, const void *raw, void *image, sar_stream stream) {
+    if (!p) return fail(SAR_ERR_INVALID_ARG, "plan is NULL");
+    if (!raw || !image) return fail(SAR_ERR_INVALID_ARG, "raw or image is NULL");
+    const size_t bytes = sizeof(float2) * (size_t)(p->n_az * p->n_range);
+    cudaStream_t s = (cudaStream_t)stream;
+    {
+        std::lock_guard<std::mutex> lk(p->host_mu);
+        if (!p->stage_raw) {
+            if (cudaMalloc(&p->stage_raw, bytes) != cudaSuccess || cudaMalloc(&p->stage_img, bytes) != cudaSuccess) {
+                cudaGetLastError();
+                if (p->stage_raw) cudaFree(p->stage_raw);
+                p->stage_raw = p->stage_img = nullptr;
+                return fail(SAR_ERR_OUT_OF_MEMORY, "staging buffers (2 x %zu bytes)", bytes);
+            }
+        }
+    }
+    SAR_CUDA(cudaMemcpyAsync(p->stage_raw, raw, bytes, cudaMemcpyHostToDevice, s), "host-to-device copy");
+    sar_status st = sar_rda_process(p, p->stage_raw, p->stage_img, stream);
+    if (st != SAR_OK) return st;
+    SAR_CUDA(cudaMemcpyAsync(image, p->stage_img, bytes, cudaMemcpyDeviceToHost, s), "device-to-host copy");
+    SAR_CUDA(cudaStreamSynchronize(s), "stream synchronise");
+    return SAR_OK;
+}
+
+sar_status sar_fft_lines(int64_t n, int64_t n_lines, const void *in, void *out, int inverse, sar_stream stream) {
+    sar_status st;
+    if ((st = check_length(n, "n")) != SAR_OK) return st;
+    if (n_lines < 0) return fail(SAR_ERR_INVALID_ARG, "n_lines < 0");
+    if (n_lines == 0) return SAR_OK;
+    if ((st = check_device_ptr(in, "in")) != SAR_OK) return st;
+    if ((st = check_device_ptr(out, "out")) != SAR_OK) return st;
+    const SchedDesc *d = sar::default_schedule((int)n);
+    float2 *tw = nullptr;
+    if ((st = cached_twiddles(d, &tw)) != SAR_OK) return st;
+    // lines are independent, each thread group reads its whole line before
+    // writing it: in == out is safe; partial overlap between lines is not
+    if (in != out && overlaps(in, out, sizeof(float2) * (size_t)(n * n_lines)))
+        return fail(SAR_ERR_INVALID_ARG, "in and out partially overlap");
+    cudaError_t e = d->dft((const float2 *)in, (float2 *)out, n_lines, n, (int)n, tw, inverse ? 1 : 0,
+                           (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fft launch");
+    return SAR_OK;
+}
+
+sar_status sar_make_lfm_spectrum(int64_t n, int64_t n_chirp, double tbp, void *out, sar_stream stream) {
+    sar_status st;
+    if ((st = check_length(n, "n")) != SAR_OK) return st;
+    if (n_chirp < 1 || n_chirp > n) return fail(SAR_ERR_INVALID_ARG, "n_chirp must be in [1, n]");
+    if (!(tbp > 0.0)) return fail(SAR_ERR_INVALID_ARG, "tbp must be > 0");
+    if ((st = check_device_ptr(out, "out")) != SAR_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = sar::make_lfm_line((int)n, (int)n_chirp, tbp, (float2 *)out, s);
+    if (e != cudaSuccess) return cuda_fail(e, "chirp launch");
+    if ((st = sar_fft_lines(n, 1, out, out, 0, stream)) != SAR_OK) return st;
+    e = sar::conjugate((float2 *)out, (int)n, s);
+    if (e != cudaSuccess) return cuda_fail(e, "conjugate launch");
+    return SAR_OK;
+}
+
+sar_status sar_transpose(int64_t rows, int64_t cols, const void *in, void *out, sar_stream stream) {
+    if (rows < 1 || cols < 1) return fail(SAR_ERR_INVALID_ARG, "rows and cols must be >= 1");
+    sar_status st;
+    if ((st = check_device_ptr(in, "in")) != SAR_OK) return st;
+    if ((st = check_device_ptr(out, "out")) != SAR_OK) return st;
+    if (overlaps(in, out, sizeof(float2) * (size_t)(rows * cols)))
+        return fail(SAR_ERR_INVALID_ARG, "in and out overlap");
+    cudaError_t e = sar::launch_transpose((const float2 *)in, (float2 *)out, rows, cols, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "transpose launch");
+    return SAR_OK;
+}
+
+sar_status sar_sync(sar_stream stream) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "device error");
+    return SAR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,79 @@
+// Plan-time tables: FP64 twiddle and chirp phases rounded to FP32, and the
+// matched filter permuted into the fused kernel's register order.
+#include "tables.h"
+
+namespace sar {
+
+// tw[r*S + lo] = exp(-2 pi i lo r / M) for r in [0, R), lo in [0, S).
+// The argument 2*lo*r/M is an exact dyadic rational in FP64; sincospi()
+// evaluates the phase in FP64 and the result is rounded once to FP32.
+__global__ void twiddle_table_kernel(float2 *tw, int R, int S, int M) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= R * S) return;
+    const int r = i / S, lo = i % S;
+    const long long e = ((long long)lo * r) % M;
+    double s, c;
+    sincospi(-2.0 * (double)e / (double)M, &s, &c);
+    tw[i] = make_float2((float)c, (float)s);
+}
+
+// One length-n line holding the chirp c(m) = exp(i pi K m^2), K = tbp/nc^2,
+// m = -nc/2 ... nc/2 - 1, at position m mod n; zero elsewhere.  The phase in
+// units of pi, tbp*m^2/nc^2, is reduced modulo 2 in FP64 before sincospi().
+__global__ void lfm_line_kernel(float2 *line, int n, int nc, double tbp) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int half = nc / 2;
+    long long m;
+    bool on = false;
+    if (p < nc - half) { m = p; on = true; }
+    else if (p >= n - half) { m = (long long)p - n; on = true; }
+    if (!on) { line[p] = make_float2(0.f, 0.f); return; }
+    const double nc2 = (double)nc * (double)nc;
+    const double x = fmod(tbp * (double)(m * m), 2.0 * nc2) / nc2;
+    double s, c;
+    sincospi(x, &s, &c);
+    line[p] = make_float2((float)c, (float)s);
+}
+
+__global__ void conj_kernel(float2 *x, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i].y = -x[i].y;
+}
+
+// dst[i] = H[idx[i]] * scale   (scale = 1/N, a power of two: exact)
+__global__ void gather_scale_kernel(float2 *dst, const float2 *H, const int32_t *idx, int n, float scale) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float2 h = H[idx[i]];
+    dst[i] = make_float2(h.x * scale, h.y * scale);
+}
+
+cudaError_t build_twiddles(const SchedDesc &d, float2 *tw, cudaStream_t st) {
+    const int S1 = d.n / d.r1;
+    int total = d.r1 * S1;
+    twiddle_table_kernel<<<(total + 255) / 256, 256, 0, st>>>(tw, d.r1, S1, d.n);
+    if (d.r3 > 1) {
+        const int S2 = S1 / d.r2;
+        const int t2 = d.r2 * S2;
+        twiddle_table_kernel<<<(t2 + 255) / 256, 256, 0, st>>>(tw + total, d.r2, S2, S1);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t build_filter(const SchedDesc &d, const float2 *H, float2 *filt, int32_t *idx_dev, cudaStream_t st) {
+    gather_scale_kernel<<<(d.n + 255) / 256, 256, 0, st>>>(filt, H, idx_dev, d.n, 1.0f / (float)d.n);
+    return cudaGetLastError();
+}
+
+cudaError_t make_lfm_line(int n, int nc, double tbp, float2 *out, cudaStream_t st) {
+    lfm_line_kernel<<<(n + 255) / 256, 256, 0, st>>>(out, n, nc, tbp);
+    return cudaGetLastError();
+}
+
+cudaError_t conjugate(float2 *x, int n, cudaStream_t st) {
+    conj_kernel<<<(n + 255) / 256, 256, 0, st>>>(x, n);
+    return cudaGetLastError();
+}
+
+}  // namespace sar

@@ -1,0 +1,11 @@
+// Plan-time table builders (device side).
+#pragma once
+#include "registry.h"
+
+namespace sar {
+cudaError_t build_twiddles(const SchedDesc &d, float2 *tw, cudaStream_t st);
+cudaError_t build_filter(const SchedDesc &d, const float2 *H, float2 *filt, int32_t *idx_dev, cudaStream_t st);
+cudaError_t make_lfm_line(int n, int nc, double tbp, float2 *out, cudaStream_t st);
+cudaError_t conjugate(float2 *x, int n, cudaStream_t st);
+cudaError_t launch_transpose(const float2 *in, float2 *out, int64_t rows, int64_t cols, cudaStream_t st);
+}  // namespace sar

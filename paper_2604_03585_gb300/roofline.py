@@ -1,0 +1,47 @@
+"""Algorithmic traffic and FLOP conventions used to report the kernels.
+
+* FFT FLOP convention (Table I of the paper): an N-point complex FFT counts
+  5 N log2 N flops; GFLOPS = 5 N log2 N / t.
+* Fused line compression (Sec. II-B): two transforms plus the spectrum
+  multiply, 2 * 5 N log2 N + 6 N flops per line.
+* Algorithmic HBM bytes: a fused pass reads and writes every complex64
+  sample once (16 bytes per sample, Sec. II-B: two transfers per line); the
+  corner turn also reads and writes every sample once.  Filters and twiddles
+  (at most 128 KiB, reused by every line from L2) are not counted.
+
+Pure host arithmetic; importing this module needs neither torch nor a GPU.
+"""
+from __future__ import annotations
+
+import math
+
+C64 = 8  # bytes per complex64 sample
+
+
+def fft_flops(n: int) -> float:
+    return 5.0 * n * math.log2(n)
+
+
+def fft_gflops(n: int, seconds_per_fft: float) -> float:
+    return fft_flops(n) / seconds_per_fft / 1e9
+
+
+def fused_line_flops(n: int) -> float:
+    return 2.0 * fft_flops(n) + 6.0 * n
+
+
+def fused_pass_bytes(n_lines: int, n: int) -> int:
+    return 2 * C64 * n_lines * n
+
+
+def corner_turn_bytes(rows: int, cols: int) -> int:
+    return 2 * C64 * rows * cols
+
+
+def rda_bytes(n_az: int, n_range: int) -> int:
+    """Three passes (range, corner turn, azimuth): 48 bytes per sample."""
+    return fused_pass_bytes(n_az, n_range) + corner_turn_bytes(n_az, n_range) + fused_pass_bytes(n_range, n_az)
+
+
+def rda_flops(n_az: int, n_range: int) -> float:
+    return n_az * fused_line_flops(n_range) + n_range * fused_line_flops(n_az)

@@ -1,0 +1,92 @@
+"""CPU-side checks of the product library: it builds, loads, exports every
+entry point that include/sar.h declares, and rejects bad arguments before
+touching the GPU.  Also the reporting conventions against the paper's tables."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def sar():
+    from paper_2604_03585_gb300 import build as b
+    b.build()
+    import paper_2604_03585_gb300 as sar
+    return sar
+
+
+def header_symbols():
+    text = open(os.path.join(ROOT, "include", "sar.h")).read()
+    return sorted(set(re.findall(r"SAR_API\s+[\w\s\*]+?\b(sar_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    syms = header_symbols()
+    for name in ("sar_plan_create", "sar_plan_destroy", "sar_range_compress", "sar_corner_turn",
+                 "sar_azimuth_compress", "sar_rda_process"):
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(sar):
+    lib = sar.library()
+    missing = [s for s in header_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+    assert set(header_symbols()) == set(sar.EXPORTS)
+
+
+def test_argument_errors_without_gpu(sar):
+    lib = sar.library()
+    import ctypes
+    # NULL out-pointer
+    assert lib.sar_plan_create(256, 256, None, None) == sar.SAR_ERR_INVALID_ARG
+    f = sar.sar_filters(None, None, 0, 0)
+    h = ctypes.c_void_p()
+    # unsupported sizes are refused before any device call
+    assert lib.sar_plan_create(300, 256, ctypes.byref(f), ctypes.byref(h)) == sar.SAR_ERR_UNSUPPORTED
+    assert lib.sar_plan_create(256, 32768, ctypes.byref(f), ctypes.byref(h)) == sar.SAR_ERR_UNSUPPORTED
+    assert lib.sar_plan_create(0, 256, ctypes.byref(f), ctypes.byref(h)) == sar.SAR_ERR_INVALID_ARG
+    assert "n_range" in sar.sar_last_error()
+    f2 = sar.sar_filters(None, None, 0, 1)
+    assert lib.sar_plan_create(256, 256, ctypes.byref(f2), ctypes.byref(h)) == sar.SAR_ERR_INVALID_ARG
+    f3 = sar.sar_filters(None, None, 7, 0)
+    assert lib.sar_plan_create(256, 256, ctypes.byref(f3), ctypes.byref(h)) == sar.SAR_ERR_UNSUPPORTED
+    assert h.value is None
+    assert lib.sar_fft_lines(100, 1, None, None, 0, None) == sar.SAR_ERR_UNSUPPORTED
+    assert lib.sar_fft_lines(256, -1, None, None, 0, None) == sar.SAR_ERR_INVALID_ARG
+    assert lib.sar_fft_lines(256, 0, None, None, 0, None) == sar.SAR_OK   # nothing to do
+    assert lib.sar_make_lfm_spectrum(256, 0, 1.0, None, None) == sar.SAR_ERR_INVALID_ARG
+    assert lib.sar_make_lfm_spectrum(256, 64, -1.0, None, None) == sar.SAR_ERR_INVALID_ARG
+    assert lib.sar_transpose(0, 4, None, None, None) == sar.SAR_ERR_INVALID_ARG
+    for fn in ("sar_range_compress", "sar_azimuth_compress"):
+        assert getattr(lib, fn)(None, None, None) == sar.SAR_ERR_INVALID_ARG
+    assert lib.sar_rda_process(None, None, None, None) == sar.SAR_ERR_INVALID_ARG
+    assert lib.sar_plan_destroy(None) == sar.SAR_OK
+    assert "sm_103a" in sar.sar_version()
+
+
+def _golden(name):
+    rows = []
+    for line in open(os.path.join(ROOT, "tests", "golden", name)):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            rows.append(line.split())
+    return rows
+
+
+def test_flop_convention_reproduces_table1():
+    from paper_2604_03585_gb300 import roofline
+    for _, gflops, us in _golden("table1_fft_gflops.txt"):
+        assert round(roofline.fft_gflops(4096, float(us) * 1e-6)) == int(gflops)
+
+
+def test_traffic_convention_reproduces_range_step():
+    from paper_2604_03585_gb300 import roofline
+    (n_lines, n, total_ms, us_line, gbs, min_ms), = _golden("table3_range_step.txt")
+    n_lines, n = int(n_lines), int(n)
+    assert abs(float(total_ms) * 1e3 / n_lines - float(us_line)) < 0.05
+    t_min = roofline.fused_pass_bytes(n_lines, n) / (float(gbs) * 1e9) * 1e3
+    assert abs(t_min - float(min_ms)) < 0.1
+    assert roofline.rda_bytes(4096, 4096) == 805306368
+    assert roofline.fused_line_flops(4096) == 516096

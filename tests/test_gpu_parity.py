@@ -1,0 +1,338 @@
+"""GPU parity: every entry point of the C-ABI against the FP64 oracle.
+
+Tolerances (relative L2 over the compared array, FP64):
+* one FP32 FFT of length N <= 16384: 2e-6 -- FP32 unit roundoff 6e-8 times
+  an error growth of order log2 N for a Cooley-Tukey transform with accurate
+  twiddles, with margin;
+* one fused line compression (two transforms + multiply): 4e-6;
+* a whole image (three passes): 2e-5, the acceptance bound for images, with
+  compressed peaks at exactly the planted positions and PSLR / ISLR / SNR
+  within 0.05 dB of the oracle's;
+* the corner turn is a copy: bit-exact.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import sarsim
+from oracle import metrics as M
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+NS = [256, 512, 1024, 2048, 4096, 8192, 16384]
+NTHREADS = max(1, os.cpu_count() or 1)
+
+
+@pytest.fixture(scope="module")
+def sar():
+    import paper_2604_03585_gb300 as sar   # must load: no fallback on a GPU machine
+    assert torch.cuda.is_available(), "gpu tests need a CUDA device"
+    torch.cuda.set_device(0)
+    return sar
+
+
+@pytest.fixture(scope="module")
+def orc():
+    return oracle.default()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rand_c64(count, seed, stream=7):
+    return sarsim.complex_gaussian(seed, stream, count, 1.0)
+
+
+def empty_c64(*shape):
+    return torch.empty(shape, dtype=torch.complex64, device="cuda")
+
+
+# ---------------------------------------------------------------------------
+# the line FFT engine on its own
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", NS)
+@pytest.mark.parametrize("inverse", [False, True], ids=["fwd", "inv"])
+def test_fft_lines_vs_oracle(sar, orc, n, inverse):
+    n_lines = 37 if n <= 4096 else 5          # not a multiple of the lines per block
+    x = rand_c64(n_lines * n, seed=n).reshape(n_lines, n)
+    y = empty_c64(n_lines, n)
+    sar.sar_fft_lines(n, n_lines, dev(x), y, inverse)
+    got = host(y)
+    for l in range(n_lines):
+        ref = orc.fft(x[l], inverse=inverse)
+        assert M.rel_l2(got[l], ref) < 2e-6, (n, l)
+
+
+@pytest.mark.parametrize("n", [256, 4096, 16384])
+def test_fft_in_place_equals_out_of_place(sar, n):
+    x = dev(rand_c64(3 * n, seed=5).reshape(3, n))
+    y = empty_c64(3, n)
+    sar.sar_fft_lines(n, 3, x, y)
+    sar.sar_fft_lines(n, 3, x, x)
+    torch.cuda.synchronize()
+    assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("n,nc,tbp", [(256, 64, 32.0), (256, 64, 16.0), (4096, 512, 256.0),
+                                      (4096, 1024, 128.0), (16384, 2048, 1024.0), (1024, 1024, 512.0)])
+def test_lfm_spectrum_vs_oracle(sar, orc, n, nc, tbp):
+    out = empty_c64(n)
+    sar.sar_make_lfm_spectrum(n, nc, tbp, out)
+    ref = orc.matched_filter(n, sarsim.lfm_chirp(nc, tbp))
+    assert M.rel_l2(host(out), ref) < 2e-6
+
+
+# ---------------------------------------------------------------------------
+# the fused passes
+# ---------------------------------------------------------------------------
+
+def make_plan(sar, n_range, n_az, Hr, Ha):
+    return sar.sar_plan_create(n_range, n_az, dev(Hr.astype(np.complex64)), dev(Ha.astype(np.complex64)))
+
+
+@pytest.mark.parametrize("n", NS)
+def test_range_compress_vs_oracle(sar, orc, n):
+    n_az = 256 if n <= 4096 else 64
+    Hr = orc.matched_filter(n, sarsim.lfm_chirp(n // 8, n / 16)).astype(np.complex64)
+    Ha = rand_c64(256, seed=3)
+    plan = make_plan(sar, n, 256, Hr, Ha)
+    x = rand_c64(n_az * n, seed=11 + n).reshape(n_az, n)
+    # a plan for n_az = 256 lines; compress only the first n_az rows' worth by
+    # building the data with exactly plan.n_az rows
+    if n_az != 256:
+        plan.destroy()
+        plan = make_plan(sar, n, 256, Hr, Ha)
+        x = rand_c64(256 * n, seed=11 + n).reshape(256, n)
+    xd = dev(x)
+    sar.sar_range_compress(plan, xd)
+    got = host(xd)
+    ref = orc.compress_lines(x, Hr.astype(np.complex128), nthreads=NTHREADS)
+    assert M.rel_l2(got, ref) < 4e-6
+    plan.destroy()
+
+
+@pytest.mark.parametrize("n", NS)
+def test_azimuth_compress_vs_oracle(sar, orc, n):
+    Ha = rand_c64(n, seed=21 + n)                     # an arbitrary spectrum, not a chirp
+    Hr = rand_c64(256, seed=4)
+    plan = make_plan(sar, 256, n, Hr, Ha)
+    x = rand_c64(256 * n, seed=31 + n).reshape(256, n)
+    xd = dev(x)
+    sar.sar_azimuth_compress(plan, xd)
+    got = host(xd)
+    ref = orc.compress_lines(x, Ha.astype(np.complex128), nthreads=NTHREADS)
+    assert M.rel_l2(got, ref) < 4e-6
+    plan.destroy()
+
+
+# ---------------------------------------------------------------------------
+# the corner turn: bit-exact
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("rows,cols", [(1, 1), (1, 7), (7, 1), (33, 65), (17, 130), (1000, 3),
+                                       (256, 256), (4096, 4096), (512, 16384), (3000, 1001)])
+def test_transpose_bit_exact(sar, rows, cols):
+    x = torch.randn(rows, cols, dtype=torch.complex64, device="cuda")
+    y = empty_c64(cols, rows)
+    sar.sar_transpose(rows, cols, x, y)
+    torch.cuda.synchronize()
+    assert torch.equal(y, x.t().contiguous())
+
+
+def test_corner_turn_plan_shape(sar):
+    n_az, n_r = 512, 2048
+    plan = make_plan(sar, n_r, n_az, rand_c64(n_r, 1), rand_c64(n_az, 2))
+    x = torch.randn(n_az, n_r, dtype=torch.complex64, device="cuda")
+    y = empty_c64(n_r, n_az)
+    sar.sar_corner_turn(plan, x, y)
+    torch.cuda.synchronize()
+    assert torch.equal(y, x.t().contiguous())
+    plan.destroy()
+
+
+# ---------------------------------------------------------------------------
+# whole scenes
+# ---------------------------------------------------------------------------
+
+def gpu_filters(sar, spec):
+    Hr = empty_c64(spec.n_range)
+    Ha = empty_c64(spec.az_len)
+    sar.sar_make_lfm_spectrum(spec.n_range, *spec.range_chirp, Hr)
+    sar.sar_make_lfm_spectrum(spec.az_len, *spec.az_chirp, Ha)
+    return Hr, Ha
+
+
+def oracle_filters(orc, spec):
+    return (orc.matched_filter(spec.n_range, sarsim.lfm_chirp(*spec.range_chirp)),
+            orc.matched_filter(spec.az_len, sarsim.lfm_chirp(*spec.az_chirp)))
+
+
+def check_image(img, ref, spec, quality=True):
+    assert img.shape == ref.shape == (spec.n_range, spec.n_az)
+    err = M.rel_l2(img, ref)
+    assert err <= 2e-5, err
+    tg = [(r0, a0) for (a0, r0) in spec.targets]
+    for t in tg:
+        assert M.peak(img, t) == t
+        assert M.peak(ref, t) == t
+    if quality:
+        qg, qr = M.quality(img, tg), M.quality(ref, tg)
+        for a, b in zip(qg["targets"], qr["targets"]):
+            assert a["pos"] == b["pos"]
+            for k in ("pslr_axis0", "pslr_axis1", "islr_axis0", "islr_axis1", "snr"):
+                assert abs(a[k] - b[k]) <= 0.05, (k, a[k], b[k])
+    return err
+
+
+def run_scene(sar, spec, Hr, Ha):
+    raw = sarsim.echo(spec)
+    plan = sar.sar_plan_create(spec.n_range, spec.n_az, Hr, Ha)
+    raw_d = dev(raw)
+    img_d = empty_c64(spec.n_range, spec.n_az)
+    sar.sar_rda_process(plan, raw_d, img_d)
+    img = host(img_d)
+    plan.destroy()
+    return raw, img
+
+
+def test_scene_256_gpu_filters(sar, orc):
+    spec = sarsim.scene_256()
+    Hr, Ha = gpu_filters(sar, spec)
+    raw, img = run_scene(sar, spec, Hr, Ha)
+    ref = orc.rda(raw, *oracle_filters(orc, spec))
+    check_image(img, ref, spec)
+
+
+def test_scene_256_shared_filters(sar, orc):
+    """Same complex64 filter spectra on both sides: isolates the compressor."""
+    spec = sarsim.scene_256()
+    Hr, Ha = (h.astype(np.complex64) for h in oracle_filters(orc, spec))
+    raw, img = run_scene(sar, spec, dev(Hr), dev(Ha))
+    ref = orc.rda(raw, Hr.astype(np.complex128), Ha.astype(np.complex128))
+    err = check_image(img, ref, spec)
+    assert err < 5e-6
+
+
+def test_scene_4096_full_size(sar, orc):
+    """The 4096 x 4096 workload in the benchmark's launch configuration,
+    compared with the oracle on every sample."""
+    spec = sarsim.scene_4096()
+    Hr, Ha = gpu_filters(sar, spec)
+    raw, img = run_scene(sar, spec, Hr, Ha)
+    ref = orc.rda(raw, *oracle_filters(orc, spec), nthreads=NTHREADS)
+    check_image(img, ref, spec)
+
+
+@pytest.mark.parametrize("n_az,n_range", [(512, 2048), (2048, 512), (16384, 256), (256, 16384)])
+def test_non_square_scenes(sar, orc, n_az, n_range):
+    rc, ac = sarsim.scaled_chirps(n_range, n_az)
+    tg = sarsim.place_targets(9, n_az, n_range, 3, margin_az=min(64, n_az // 8),
+                              margin_r=min(64, n_range // 8), min_sep=16)
+    spec = sarsim.SceneSpec(n_az, n_range, tg, rc, ac, 10.0, 9)
+    Hr, Ha = gpu_filters(sar, spec)
+    raw, img = run_scene(sar, spec, Hr, Ha)
+    ref = orc.rda(raw, *oracle_filters(orc, spec), nthreads=NTHREADS)
+    check_image(img, ref, spec, quality=False)
+
+
+def test_noise_free_peak_value(sar):
+    spec = sarsim.scene_256()
+    spec.snr_db = None
+    Hr, Ha = gpu_filters(sar, spec)
+    _, img = run_scene(sar, spec, Hr, Ha)
+    assert abs(img[128, 128] - 64 * 64) < 1e-4 * 64 * 64
+
+
+# ---------------------------------------------------------------------------
+# properties of the product path
+# ---------------------------------------------------------------------------
+
+def test_deterministic(sar):
+    spec = sarsim.scene_256()
+    Hr, Ha = gpu_filters(sar, spec)
+    _, a = run_scene(sar, spec, Hr, Ha)
+    _, b = run_scene(sar, spec, Hr, Ha)
+    assert np.array_equal(a, b)
+
+
+def test_host_entry_point_matches_device(sar):
+    spec = sarsim.scene_256()
+    Hr, Ha = gpu_filters(sar, spec)
+    raw, img = run_scene(sar, spec, Hr, Ha)
+    plan = sar.sar_plan_create(spec.n_range, spec.n_az, Hr, Ha)
+    raw_h = torch.from_numpy(raw).pin_memory()
+    img_h = torch.empty((spec.n_range, spec.n_az), dtype=torch.complex64).pin_memory()
+    sar.sar_rda_process_host(plan, raw_h, img_h)
+    assert np.array_equal(img_h.numpy(), img)
+    assert np.array_equal(raw_h.numpy(), raw)        # host input untouched
+    plan.destroy()
+
+
+def test_guard_bands_untouched(sar):
+    n_az, n_r, guard = 256, 512, 4096
+    plan = make_plan(sar, n_r, n_az, rand_c64(n_r, 1), rand_c64(n_az, 2))
+    canary = complex(1234.5, -987.25)
+    buf = torch.full((2 * guard + n_az * n_r,), canary, dtype=torch.complex64, device="cuda")
+    out = torch.full((2 * guard + n_az * n_r,), canary, dtype=torch.complex64, device="cuda")
+    buf[guard:guard + n_az * n_r] = torch.randn(n_az * n_r, dtype=torch.complex64, device="cuda")
+    sar.sar_rda_process(plan, buf[guard:], out[guard:])
+    torch.cuda.synchronize()
+    for b in (buf, out):
+        assert bool((b[:guard] == canary).all()) and bool((b[guard + n_az * n_r:] == canary).all())
+    plan.destroy()
+
+
+def test_bad_arguments_are_refused(sar):
+    spec = sarsim.scene_256()
+    Hr, Ha = gpu_filters(sar, spec)
+    plan = sar.sar_plan_create(256, 256, Hr, Ha)
+    good = empty_c64(256, 256)
+    other = empty_c64(256, 256)
+    host_arr = np.zeros((256, 256), np.complex64)
+    with pytest.raises(sar.SarError) as e:
+        sar.sar_range_compress(plan, host_arr)             # host memory
+    assert e.value.status == sar.SAR_ERR_INVALID_ARG
+    flat = empty_c64(256 * 256 + 1)
+    with pytest.raises(sar.SarError) as e:
+        sar.sar_range_compress(plan, flat[1:])              # 8-byte, not 16-byte, aligned
+    assert e.value.status == sar.SAR_ERR_INVALID_ARG
+    with pytest.raises(sar.SarError) as e:
+        sar.sar_rda_process(plan, good, good)                # image overlaps raw
+    assert e.value.status == sar.SAR_ERR_INVALID_ARG
+    with pytest.raises(sar.SarError) as e:
+        sar.sar_plan_create(256, 256 * 3, Hr, Ha)
+    assert e.value.status == sar.SAR_ERR_UNSUPPORTED
+    with pytest.raises(sar.SarError) as e:
+        sar.sar_plan_create(256, 32768, Hr, Ha)
+    assert e.value.status == sar.SAR_ERR_UNSUPPORTED
+    sar.sar_rda_process(plan, good, other)                   # still usable afterwards
+    sar.sar_sync()
+    plan.destroy()
+
+
+def test_allocation_failure_is_reported(sar):
+    spec = sarsim.scene_256()
+    Hr, Ha = gpu_filters(sar, spec)
+    os.environ["SAR_FAULT_INJECT_ALLOC"] = "1"
+    try:
+        with pytest.raises(sar.SarError) as e:
+            sar.sar_plan_create(256, 256, Hr, Ha)
+        assert e.value.status == sar.SAR_ERR_OUT_OF_MEMORY
+    finally:
+        del os.environ["SAR_FAULT_INJECT_ALLOC"]
+    sar.sar_plan_create(256, 256, Hr, Ha).destroy()
+
+
+def test_empty_inputs(sar):
+    sar.sar_fft_lines(256, 0, 0, 0)        # zero lines: nothing to do, no pointer needed
+    sar.sar_sync()
