@@ -10,9 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module")
-def sar():
-    from paper_2604_03585_gb300 import build as b
-    b.build()
+def sar(built_lib):
     import paper_2604_03585_gb300 as sar
     return sar
 
@@ -75,13 +73,13 @@ def _golden(name):
     return rows
 
 
-def test_flop_convention_reproduces_table1():
+def test_flop_convention_reproduces_table1(sar):
     from paper_2604_03585_gb300 import roofline
     for _, gflops, us in _golden("table1_fft_gflops.txt"):
         assert round(roofline.fft_gflops(4096, float(us) * 1e-6)) == int(gflops)
 
 
-def test_traffic_convention_reproduces_range_step():
+def test_traffic_convention_reproduces_range_step(sar):
     from paper_2604_03585_gb300 import roofline
     (n_lines, n, total_ms, us_line, gbs, min_ms), = _golden("table3_range_step.txt")
     n_lines, n = int(n_lines), int(n)
