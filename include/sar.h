@@ -149,6 +149,24 @@ SAR_API sar_status sar_make_lfm_spectrum(int64_t n, int64_t n_chirp, double tbp,
  * Exposes the line FFT engine on its own (tests, filter design). */
 SAR_API sar_status sar_fft_lines(int64_t n, int64_t n_lines, const void *in, void *out, int inverse, sar_stream stream);
 
+/* sar_fft_lines without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that must not have device memory
+ * allocated on their behalf -- work recorded inside a CUDA stream capture,
+ * real-time / on-board processors that fix their device-memory footprint at
+ * start-up, applications whose device memory belongs to a pool allocator.
+ * Same arguments and results as sar_fft_lines; it calls no cudaMalloc,
+ * cudaFree or allocating library routine.  Its twiddle table lives in one
+ * fixed device array of 32768 complex64 values (256 KiB, held by every GPU
+ * that loads the library until the process exits); every N in [256, 16384]
+ * fits, anything needing more is refused with SAR_ERR_UNSUPPORTED.  Every
+ * call rewrites that array on its stream before its FFT, and all calls share
+ * it: calls that may run at the same time on the GPU (different streams with
+ * no ordering between them) race on it, so order them.  The first call on a
+ * device looks up the array's address once; make it before any stream
+ * capture. */
+SAR_API sar_status sar_fft_lines_static(int64_t n, int64_t n_lines, const void *in, void *out, int inverse,
+                                        sar_stream stream);
+
 /* Generic corner turn of a rows x cols complex64 matrix (any sizes >= 1):
  * out[c][r] = in[r][c].  Device pointers, non-overlapping. */
 SAR_API sar_status sar_transpose(int64_t rows, int64_t cols, const void *in, void *out, sar_stream stream);

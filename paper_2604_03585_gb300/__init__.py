@@ -34,7 +34,7 @@ STATUS_NAMES = {0: "SAR_OK", 1: "SAR_ERR_INVALID_ARG", 2: "SAR_ERR_UNSUPPORTED",
 EXPORTS = ("sar_plan_create", "sar_plan_destroy", "sar_range_compress", "sar_corner_turn",
            "sar_azimuth_compress", "sar_rda_process", "sar_range_compress_oop", "sar_rda_process_oop",
            "sar_rda_process_host", "sar_make_lfm_spectrum",
-           "sar_fft_lines", "sar_transpose", "sar_sync", "sar_last_error", "sar_version")
+           "sar_fft_lines", "sar_fft_lines_static", "sar_transpose", "sar_sync", "sar_last_error", "sar_version")
 
 
 class sar_filters(ctypes.Structure):
@@ -55,6 +55,7 @@ _SIGS = {
     "sar_rda_process_host": [_vp, _vp, _vp, _vp],
     "sar_make_lfm_spectrum": [_i64, _i64, _dbl, _vp, _vp],
     "sar_fft_lines": [_i64, _i64, _vp, _vp, _int, _vp],
+    "sar_fft_lines_static": [_i64, _i64, _vp, _vp, _int, _vp],
     "sar_transpose": [_i64, _i64, _vp, _vp, _vp],
     "sar_sync": [_vp],
 }
@@ -182,6 +183,14 @@ def sar_make_lfm_spectrum(n: int, n_chirp: int, tbp: float, out, stream=None) ->
 
 def sar_fft_lines(n: int, n_lines: int, inp, out, inverse: bool = False, stream=None) -> None:
     _check(_lib.sar_fft_lines(n, n_lines, _ptr(inp), _ptr(out), 1 if inverse else 0, _stream(stream)))
+
+
+def sar_fft_lines_static(n: int, n_lines: int, inp, out, inverse: bool = False, stream=None) -> None:
+    """sar_fft_lines for callers that must not have device memory allocated
+    for them (stream capture, fixed-footprint real-time code, pool-owned
+    memory): its twiddles live in a fixed 256 KiB device array shared by all
+    calls, so concurrent calls on unordered streams race."""
+    _check(_lib.sar_fft_lines_static(n, n_lines, _ptr(inp), _ptr(out), 1 if inverse else 0, _stream(stream)))
 
 
 def sar_transpose(rows: int, cols: int, inp, out, stream=None) -> None:

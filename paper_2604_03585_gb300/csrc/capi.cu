@@ -124,6 +124,15 @@ bool fault_inject_alloc() {
 
 }  // namespace
 
+// Internal hooks for other translation units of this library: record an
+// error for sar_last_error(), and validate a device pointer the same way the
+// entry points above do.
+namespace sar {
+sar_status report_error(sar_status st, const char *msg) { return fail(st, "%s", msg); }
+sar_status validate_device_ptr(const void *p, const char *what) { return check_device_ptr(p, what); }
+sar_status validate_length(int64_t n, const char *what) { return check_length(n, what); }
+}  // namespace sar
+
 struct sar_plan_s {
     int64_t n_range = 0, n_az = 0;
     int device = 0;
