@@ -75,8 +75,14 @@ typedef struct {
     const void *range_spectrum;
     const void *az_spectrum;
     int32_t precision; /* sar_precision */
-    uint32_t flags;    /* must be 0 */
+    uint32_t flags;    /* 0 or SAR_PLAN_* bits below */
 } sar_filters;
+
+/* Plan flags.  By default sar_rda_process folds the corner turn into the
+ * range pass where the range schedule supports it (two kernels, 32 bytes of
+ * HBM traffic per sample); this flag keeps the three separate kernels of
+ * Sec. IV-A (48 bytes per sample). */
+#define SAR_PLAN_UNFOLDED_CORNER_TURN 1u
 
 /* Create a plan for an n_az x n_range scene (Sec. IV-A, the N_a x N_r data
  * matrix).  n_range and n_az: powers of two in [256, 16384].  Allocates the
@@ -105,9 +111,12 @@ SAR_API sar_status sar_corner_turn(sar_plan plan, const void *in, void *out, sar
  * IFFT(FFT(x) . H_a), in place.  data: device complex64[n_range][n_az]. */
 SAR_API sar_status sar_azimuth_compress(sar_plan plan, void *data, sar_stream stream);
 
-/* The three steps in order: range compression in place on raw, corner turn
- * raw -> image, azimuth compression in place on image.
- * raw:   device complex64[n_az][n_range], input; overwritten (range-compressed).
+/* The three steps: range compression, corner turn raw -> image, azimuth
+ * compression in place on image.  With the corner turn folded into the range
+ * pass (the default where supported) raw is only read; otherwise (flag
+ * SAR_PLAN_UNFOLDED_CORNER_TURN, or a range length without a folded kernel)
+ * raw is range-compressed in place first.
+ * raw:   device complex64[n_az][n_range], input; may be overwritten.
  * image: device complex64[n_range][n_az], output; must not overlap raw. */
 SAR_API sar_status sar_rda_process(sar_plan plan, void *raw, void *image, sar_stream stream);
 
@@ -116,9 +125,18 @@ SAR_API sar_status sar_rda_process(sar_plan plan, void *raw, void *image, sar_st
  * the in-place call, any other overlap is refused. */
 SAR_API sar_status sar_range_compress_oop(sar_plan plan, const void *in, void *out, sar_stream stream);
 
+/* Range compression with the corner turn folded into its store (Sec. IV-A
+ * steps 1 and 2 in one kernel): image[r][a] = (IFFT(FFT(raw[a]) . H_r))[r].
+ * raw: device complex64[n_az][n_range] (read only); image: device
+ * complex64[n_range][n_az].  Only for plans that fold the corner turn
+ * (sar_plan_folds_corner_turn); SAR_ERR_UNSUPPORTED otherwise. */
+SAR_API sar_status sar_range_compress_ct(sar_plan plan, const void *raw, void *image, sar_stream stream);
+
 /* The three steps leaving the raw echo intact: range compression raw -> work,
- * corner turn work -> image, azimuth compression in place on image.  Same
- * three kernels and the same HBM traffic as sar_rda_process.
+ * corner turn work -> image, azimuth compression in place on image (or, when
+ * the corner turn is folded into the range pass, raw -> image directly and
+ * work is not touched).  The same kernels and HBM traffic as
+ * sar_rda_process.
  * raw: device complex64[n_az][n_range] (read only); work: device
  * complex64[n_az][n_range] scratch owned by the caller; image: device
  * complex64[n_range][n_az].  The three buffers must not overlap. */
@@ -170,6 +188,73 @@ SAR_API sar_status sar_fft_lines_static(int64_t n, int64_t n_lines, const void *
 /* Generic corner turn of a rows x cols complex64 matrix (any sizes >= 1):
  * out[c][r] = in[r][c].  Device pointers, non-overlapping. */
 SAR_API sar_status sar_transpose(int64_t rows, int64_t cols, const void *in, void *out, sar_stream stream);
+
+/* ---- schedules and the autotuner --------------------------------------
+ * A schedule fixes how the fused line kernel of one line length N runs: the
+ * samples held per thread (E), the pass radices (N = r1*r2*r3, r3 = 1 for two
+ * passes), the lines per thread block, and the resulting block size and
+ * shared memory.  Several schedules are compiled per N; which one is fastest
+ * depends on the GPU, so a plan takes the process-wide preferred schedule of
+ * each length (the first compiled one until sar_autotune or
+ * sar_set_preferred_schedule changes it), or names one explicitly. */
+typedef struct {
+    char name[48];
+    int32_t n, e, r1, r2, r3, lines_per_block, threads_per_block, smem_bytes;
+} sar_schedule_desc;
+
+/* Number of compiled schedules, and the description of schedule `index`
+ * (0 <= index < count). */
+SAR_API int32_t sar_schedule_count(void);
+SAR_API sar_status sar_schedule_get(int32_t index, sar_schedule_desc *out);
+
+/* Make the named schedule the preferred one for its length (process-wide,
+ * thread-safe; affects plans created afterwards); if it has a folded
+ * range + corner-turn kernel it also becomes the preferred one of that
+ * kind. */
+SAR_API sar_status sar_set_preferred_schedule(const char *name);
+
+/* sar_plan_create with explicit schedules for the range and azimuth lines
+ * (NULL = the preferred schedule of that length).  SAR_ERR_INVALID_ARG if a
+ * name is unknown or belongs to another length. */
+SAR_API sar_status sar_plan_create_ex(int64_t n_range, int64_t n_az, const sar_filters *filters,
+                                      const char *range_schedule, const char *az_schedule, sar_plan *out);
+
+/* Corner-turn kernel choice (process-wide): 0 = automatic, 1 = 32 x 32
+ * tiles of 8-byte accesses, 2 = 64 x 64 tiles of 16-byte accesses (rows and
+ * columns multiples of 64).  Any other value is refused. */
+SAR_API sar_status sar_set_corner_turn_variant(int32_t variant);
+
+/* 1 if sar_rda_process of this plan folds the corner turn into the range
+ * pass (two kernels), 0 if it runs three kernels (or plan is NULL). */
+SAR_API int32_t sar_plan_folds_corner_turn(sar_plan plan);
+
+/* The schedules a plan runs. */
+SAR_API sar_status sar_plan_get_schedules(sar_plan plan, sar_schedule_desc *range, sar_schedule_desc *az);
+
+/* Time every compiled schedule of length n (reps launches each, CUDA events
+ * on `stream`, median) and make the fastest the preferred schedule of n for
+ * that kind of kernel:
+ *   kind SAR_TUNE_FUSED:    the fused line compression on n_lines lines;
+ *   kind SAR_TUNE_RANGE_CT: the range pass with the folded corner turn on
+ *                           n_lines lines (schedules that have it; n_lines a
+ *                           multiple of 4).
+ * Returns the winner and its median time in milliseconds; if all_ms is not
+ * NULL it receives each candidate's median (up to all_cap values; 0 for a
+ * schedule without that kind of kernel), in the order sar_schedule_get lists
+ * the schedules of length n.  Allocates (and frees) 2 x n_lines x n x 8 bytes
+ * of device memory and synchronises the stream; a tuning call, not for the
+ * hot path.  n_lines >= 1, reps >= 1. */
+#define SAR_TUNE_FUSED 0
+#define SAR_TUNE_RANGE_CT 1
+SAR_API sar_status sar_autotune(int64_t n, int64_t n_lines, int32_t reps, int32_t kind, sar_stream stream,
+                                sar_schedule_desc *best, float *best_ms, float *all_ms, int32_t all_cap);
+
+/* Synchronise `stream` and report whether any kernel of this plan gave up a
+ * bounded device-side wait since the last check (SAR_ERR_TIMEOUT; the lines
+ * it was processing were not written), then clear that record.  The
+ * persistent kernels bound every wait by about one second of SM clock
+ * (SAR_WAIT_CYCLES overrides it when the plan is created). */
+SAR_API sar_status sar_plan_status(sar_plan plan, sar_stream stream);
 
 /* Wait for `stream` and report any asynchronous device error. */
 SAR_API sar_status sar_sync(sar_stream stream);

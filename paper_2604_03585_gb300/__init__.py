@@ -26,15 +26,29 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 SAR_OK, SAR_ERR_INVALID_ARG, SAR_ERR_UNSUPPORTED, SAR_ERR_OUT_OF_MEMORY, SAR_ERR_CUDA, SAR_ERR_TIMEOUT = range(6)
 SAR_PREC_FP32 = 0
+SAR_PLAN_UNFOLDED_CORNER_TURN = 1
+SAR_TUNE_FUSED, SAR_TUNE_RANGE_CT = 0, 1
 
 STATUS_NAMES = {0: "SAR_OK", 1: "SAR_ERR_INVALID_ARG", 2: "SAR_ERR_UNSUPPORTED",
                 3: "SAR_ERR_OUT_OF_MEMORY", 4: "SAR_ERR_CUDA", 5: "SAR_ERR_TIMEOUT"}
 
 # every entry point declared in include/sar.h
 EXPORTS = ("sar_plan_create", "sar_plan_destroy", "sar_range_compress", "sar_corner_turn",
-           "sar_azimuth_compress", "sar_rda_process", "sar_range_compress_oop", "sar_rda_process_oop",
+           "sar_azimuth_compress", "sar_rda_process", "sar_range_compress_oop", "sar_range_compress_ct", "sar_rda_process_oop",
            "sar_rda_process_host", "sar_make_lfm_spectrum",
-           "sar_fft_lines", "sar_fft_lines_static", "sar_transpose", "sar_sync", "sar_last_error", "sar_version")
+           "sar_fft_lines", "sar_fft_lines_static", "sar_transpose", "sar_schedule_count", "sar_schedule_get",
+           "sar_set_preferred_schedule", "sar_set_corner_turn_variant", "sar_plan_create_ex", "sar_plan_get_schedules", "sar_plan_folds_corner_turn", "sar_autotune",
+           "sar_plan_status", "sar_sync", "sar_last_error", "sar_version")
+
+
+class sar_schedule_desc(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("n", ctypes.c_int32), ("e", ctypes.c_int32),
+                ("r1", ctypes.c_int32), ("r2", ctypes.c_int32), ("r3", ctypes.c_int32),
+                ("lines_per_block", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
+                ("smem_bytes", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: (getattr(self, f).decode() if f == "name" else getattr(self, f)) for f, _ in self._fields_}
 
 
 class sar_filters(ctypes.Structure):
@@ -51,6 +65,7 @@ _SIGS = {
     "sar_azimuth_compress": [_vp, _vp, _vp],
     "sar_rda_process": [_vp, _vp, _vp, _vp],
     "sar_range_compress_oop": [_vp, _vp, _vp, _vp],
+    "sar_range_compress_ct": [_vp, _vp, _vp, _vp],
     "sar_rda_process_oop": [_vp, _vp, _vp, _vp, _vp],
     "sar_rda_process_host": [_vp, _vp, _vp, _vp],
     "sar_make_lfm_spectrum": [_i64, _i64, _dbl, _vp, _vp],
@@ -58,11 +73,24 @@ _SIGS = {
     "sar_fft_lines_static": [_i64, _i64, _vp, _vp, _int, _vp],
     "sar_transpose": [_i64, _i64, _vp, _vp, _vp],
     "sar_sync": [_vp],
+    "sar_plan_status": [_vp, _vp],
+    "sar_schedule_get": [ctypes.c_int32, ctypes.POINTER(sar_schedule_desc)],
+    "sar_set_preferred_schedule": [ctypes.c_char_p],
+    "sar_set_corner_turn_variant": [ctypes.c_int32],
+    "sar_plan_create_ex": [_i64, _i64, ctypes.POINTER(sar_filters), ctypes.c_char_p, ctypes.c_char_p,
+                           ctypes.POINTER(_vp)],
+    "sar_plan_get_schedules": [_vp, ctypes.POINTER(sar_schedule_desc), ctypes.POINTER(sar_schedule_desc)],
+    "sar_autotune": [_i64, _i64, ctypes.c_int32, ctypes.c_int32, _vp, ctypes.POINTER(sar_schedule_desc),
+                     ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), ctypes.c_int32],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
     _f.argtypes = _args
     _f.restype = ctypes.c_int
+_lib.sar_plan_folds_corner_turn.restype = ctypes.c_int32
+_lib.sar_plan_folds_corner_turn.argtypes = [_vp]
+_lib.sar_schedule_count.restype = ctypes.c_int32
+_lib.sar_schedule_count.argtypes = []
 _lib.sar_last_error.restype = ctypes.c_char_p
 _lib.sar_version.restype = ctypes.c_char_p
 
@@ -141,6 +169,62 @@ def sar_plan_create(n_range: int, n_az: int, range_spectrum, az_spectrum, precis
     return Plan(h.value, n_range, n_az)
 
 
+def sar_plan_create_ex(n_range: int, n_az: int, range_spectrum, az_spectrum, range_schedule=None,
+                       az_schedule=None, precision: int = SAR_PREC_FP32, flags: int = 0) -> Plan:
+    f = sar_filters(_ptr(range_spectrum), _ptr(az_spectrum), precision, flags)
+    h = _vp()
+    enc = lambda x: None if x is None else x.encode()
+    _check(_lib.sar_plan_create_ex(n_range, n_az, ctypes.byref(f), enc(range_schedule), enc(az_schedule),
+                                   ctypes.byref(h)))
+    return Plan(h.value, n_range, n_az)
+
+
+def sar_plan_folds_corner_turn(plan) -> bool:
+    return bool(_lib.sar_plan_folds_corner_turn(_h(plan)))
+
+
+def sar_plan_get_schedules(plan) -> tuple:
+    r, a = sar_schedule_desc(), sar_schedule_desc()
+    _check(_lib.sar_plan_get_schedules(_h(plan), ctypes.byref(r), ctypes.byref(a)))
+    return r.as_dict(), a.as_dict()
+
+
+def sar_schedule_count() -> int:
+    return int(_lib.sar_schedule_count())
+
+
+def sar_schedule_get(index: int) -> dict:
+    d = sar_schedule_desc()
+    _check(_lib.sar_schedule_get(index, ctypes.byref(d)))
+    return d.as_dict()
+
+
+def schedules(n: int | None = None) -> list:
+    out = [sar_schedule_get(i) for i in range(sar_schedule_count())]
+    return [d for d in out if n is None or d["n"] == n]
+
+
+def sar_set_preferred_schedule(name: str) -> None:
+    _check(_lib.sar_set_preferred_schedule(name.encode()))
+
+
+def sar_set_corner_turn_variant(variant: int) -> None:
+    _check(_lib.sar_set_corner_turn_variant(variant))
+
+
+def sar_autotune(n: int, n_lines: int, reps: int = 20, stream=None, kind: int = SAR_TUNE_FUSED) -> tuple:
+    """Time every schedule of length n for one kind of kernel; returns (best
+    schedule, best ms, {schedule name: median ms}), leaving out schedules
+    without that kind of kernel."""
+    d = sar_schedule_desc()
+    ms = ctypes.c_float()
+    cands = schedules(n)
+    arr = (ctypes.c_float * max(1, len(cands)))()
+    _check(_lib.sar_autotune(n, n_lines, reps, kind, _stream(stream), ctypes.byref(d), ctypes.byref(ms), arr,
+                             len(cands)))
+    return d.as_dict(), float(ms.value), {c["name"]: float(arr[i]) for i, c in enumerate(cands) if arr[i] > 0}
+
+
 def sar_plan_destroy(plan: Plan) -> None:
     plan.destroy()
 
@@ -169,6 +253,10 @@ def sar_range_compress_oop(plan, inp, out, stream=None) -> None:
     _check(_lib.sar_range_compress_oop(_h(plan), _ptr(inp), _ptr(out), _stream(stream)))
 
 
+def sar_range_compress_ct(plan, raw, image, stream=None) -> None:
+    _check(_lib.sar_range_compress_ct(_h(plan), _ptr(raw), _ptr(image), _stream(stream)))
+
+
 def sar_rda_process_oop(plan, raw, work, image, stream=None) -> None:
     _check(_lib.sar_rda_process_oop(_h(plan), _ptr(raw), _ptr(work), _ptr(image), _stream(stream)))
 
@@ -195,6 +283,11 @@ def sar_fft_lines_static(n: int, n_lines: int, inp, out, inverse: bool = False, 
 
 def sar_transpose(rows: int, cols: int, inp, out, stream=None) -> None:
     _check(_lib.sar_transpose(rows, cols, _ptr(inp), _ptr(out), _stream(stream)))
+
+
+def sar_plan_status(plan, stream=None) -> None:
+    """Raise SarError(SAR_ERR_TIMEOUT) if a kernel of the plan gave up a bounded wait."""
+    _check(_lib.sar_plan_status(_h(plan), _stream(stream)))
 
 
 def sar_sync(stream=None) -> None:

@@ -1,6 +1,7 @@
 // C-ABI of libsar: plan lifecycle, argument validation and the entry points
 // declared in include/sar.h.  All compute runs in this library's kernels;
 // there is no host or library fallback.
+#include <algorithm>
 #include <mutex>
 #include <new>
 #include <stdarg.h>
@@ -122,6 +123,22 @@ bool fault_inject_alloc() {
     return v && v[0] == '1';
 }
 
+// Bound of every device-side wait of a plan's kernels: about one second at
+// the GB300's maximum SM clock, or SAR_WAIT_CYCLES.
+long long plan_wait_cycles() {
+    const char *v = getenv("SAR_WAIT_CYCLES");
+    long long c = v ? atoll(v) : 0;
+    return c > 0 ? c : 2000000000LL;
+}
+
+// Test hook (host-side fault injection): SAR_FAULT_INJECT_SKIP_LINE=<l> makes
+// the persistent kernels of plans created while it is set never start the
+// copy of line l, so that line's bounded wait runs out.
+int64_t plan_skip_line() {
+    const char *v = getenv("SAR_FAULT_INJECT_SKIP_LINE");
+    return v ? atoll(v) : -1;
+}
+
 }  // namespace
 
 // Internal hooks for other translation units of this library: record an
@@ -137,6 +154,9 @@ struct sar_plan_s {
     int64_t n_range = 0, n_az = 0;
     int device = 0;
     LinePlan range, az;
+    int *status = nullptr;  // device word written by timed-out kernels (0 = fine)
+    bool fold = false;      // range pass writes the corner-turned image itself
+    sar::FusedCtl ctl{};
     void *block = nullptr;  // one device allocation holding every table
     std::mutex host_mu;
     void *stage_raw = nullptr, *stage_img = nullptr;  // lazily, for the host-buffer entry point
@@ -149,20 +169,35 @@ const char *sar_last_error(void) { return g_last_error.c_str(); }
 const char *sar_version(void) { return "sar-gb300 0.1 (sm_103a)"; }
 
 sar_status sar_plan_create(int64_t n_range, int64_t n_az, const sar_filters *filters, sar_plan *out) {
+    return sar_plan_create_ex(n_range, n_az, filters, nullptr, nullptr, out);
+}
+
+sar_status sar_plan_create_ex(int64_t n_range, int64_t n_az, const sar_filters *filters, const char *range_schedule,
+                              const char *az_schedule, sar_plan *out) {
     if (!out) return fail(SAR_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!filters) return fail(SAR_ERR_INVALID_ARG, "filters is NULL");
     sar_status st;
     if ((st = check_length(n_range, "n_range")) != SAR_OK) return st;
     if ((st = check_length(n_az, "n_az")) != SAR_OK) return st;
-    if (filters->flags != 0) return fail(SAR_ERR_INVALID_ARG, "filters->flags must be 0");
+    if (filters->flags & ~SAR_PLAN_UNFOLDED_CORNER_TURN)
+        return fail(SAR_ERR_INVALID_ARG, "filters->flags has unknown bits 0x%x", filters->flags);
     if (filters->precision != SAR_PREC_FP32)
         return fail(SAR_ERR_UNSUPPORTED, "precision %d is not available", (int)filters->precision);
     if ((st = check_device_ptr(filters->range_spectrum, "filters->range_spectrum")) != SAR_OK) return st;
     if ((st = check_device_ptr(filters->az_spectrum, "filters->az_spectrum")) != SAR_OK) return st;
 
-    const SchedDesc *dr = sar::default_schedule((int)n_range);
-    const SchedDesc *da = sar::default_schedule((int)n_az);
+    const bool want_fold = !(filters->flags & SAR_PLAN_UNFOLDED_CORNER_TURN);
+    const SchedDesc *dr = range_schedule ? sar::find_schedule(range_schedule) : nullptr;
+    if (!range_schedule) {
+        dr = want_fold ? sar::default_ct_schedule((int)n_range) : nullptr;
+        if (!dr || n_az % dr->ct_lines) dr = sar::default_schedule((int)n_range);
+    }
+    const SchedDesc *da = az_schedule ? sar::find_schedule(az_schedule) : sar::default_schedule((int)n_az);
+    if (range_schedule && (!dr || dr->n != n_range))
+        return fail(SAR_ERR_INVALID_ARG, "range schedule '%s' is unknown or not for n_range", range_schedule);
+    if (az_schedule && (!da || da->n != n_az))
+        return fail(SAR_ERR_INVALID_ARG, "azimuth schedule '%s' is unknown or not for n_az", az_schedule);
     if (!dr || !da) return fail(SAR_ERR_UNSUPPORTED, "no compiled schedule for this size");
 
     sar_plan p = new (std::nothrow) sar_plan_s;
@@ -172,6 +207,7 @@ sar_status sar_plan_create(int64_t n_range, int64_t n_az, const sar_filters *fil
     cudaGetDevice(&p->device);
     p->range.sched = dr;
     p->az.sched = da;
+    p->fold = want_fold && dr->fused_ct && n_az % dr->ct_lines == 0;
 
     // one block: filt_r | tw_r | filt_a | tw_a | idx (int32, max n)
     const size_t o_fr = 0;
@@ -179,7 +215,8 @@ sar_status sar_plan_create(int64_t n_range, int64_t n_az, const sar_filters *fil
     const size_t o_fa = o_tr + align_up(sizeof(float2) * (size_t)dr->tw_elems);
     const size_t o_ta = o_fa + align_up(sizeof(float2) * (size_t)n_az);
     const size_t o_ix = o_ta + align_up(sizeof(float2) * (size_t)da->tw_elems);
-    const size_t total = o_ix + align_up(sizeof(int32_t) * (size_t)(n_range > n_az ? n_range : n_az));
+    const size_t o_st = o_ix + align_up(sizeof(int32_t) * (size_t)(n_range > n_az ? n_range : n_az));
+    const size_t total = o_st + 256;
     cudaError_t e = fault_inject_alloc() ? cudaErrorMemoryAllocation : cudaMalloc(&p->block, total);
     if (e != cudaSuccess) {
         if (e != cudaErrorMemoryAllocation) cudaGetLastError();
@@ -193,6 +230,8 @@ sar_status sar_plan_create(int64_t n_range, int64_t n_az, const sar_filters *fil
     p->az.filt = (float2 *)(b + o_fa);
     p->az.tw = (float2 *)(b + o_ta);
     int32_t *idx_dev = (int32_t *)(b + o_ix);
+    p->status = (int *)(b + o_st);
+    p->ctl = sar::FusedCtl{p->status, plan_wait_cycles(), plan_skip_line()};
 
     cudaStream_t s = nullptr;
     std::vector<int32_t> idx;
@@ -204,6 +243,7 @@ sar_status sar_plan_create(int64_t n_range, int64_t n_az, const sar_filters *fil
     };
     if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess)
         return cleanup_fail(e, "cudaStreamCreate");
+    if ((e = cudaMemsetAsync(p->status, 0, sizeof(int), s)) != cudaSuccess) return cleanup_fail(e, "status word");
     // the caller's spectra were produced on the legacy stream or another one:
     // wait for the device once before reading them
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cleanup_fail(e, "cudaDeviceSynchronize");
@@ -229,6 +269,140 @@ sar_status sar_plan_create(int64_t n_range, int64_t n_az, const sar_filters *fil
     return SAR_OK;
 }
 
+static void describe(const SchedDesc &d, sar_schedule_desc *o) {
+    memset(o, 0, sizeof(*o));
+    strncpy(o->name, d.name, sizeof(o->name) - 1);
+    o->n = d.n;
+    o->e = d.e;
+    o->r1 = d.r1;
+    o->r2 = d.r2;
+    o->r3 = d.r3;
+    o->lines_per_block = d.lpb;
+    o->threads_per_block = d.threads;
+    o->smem_bytes = d.smem_bytes;
+}
+
+int32_t sar_schedule_count(void) { return sar::schedule_count(); }
+
+sar_status sar_schedule_get(int32_t index, sar_schedule_desc *out) {
+    const SchedDesc *d = sar::schedule_at(index);
+    if (!d || !out) return fail(SAR_ERR_INVALID_ARG, "schedule index %d out of range or out is NULL", index);
+    describe(*d, out);
+    return SAR_OK;
+}
+
+sar_status sar_set_preferred_schedule(const char *name) {
+    const SchedDesc *d = name ? sar::find_schedule(name) : nullptr;
+    if (!d) return fail(SAR_ERR_INVALID_ARG, "unknown schedule '%s'", name ? name : "(null)");
+    sar::set_preferred_schedule(d);
+    return SAR_OK;
+}
+
+sar_status sar_set_corner_turn_variant(int32_t v) {
+    if (v < 0 || v > 2) return fail(SAR_ERR_INVALID_ARG, "corner-turn variant %d is not 0, 1 or 2", v);
+    sar::set_corner_turn_variant(v);
+    return SAR_OK;
+}
+
+int32_t sar_plan_folds_corner_turn(sar_plan p) { return p && p->fold ? 1 : 0; }
+
+sar_status sar_plan_get_schedules(sar_plan p, sar_schedule_desc *range, sar_schedule_desc *az) {
+    if (!p) return fail(SAR_ERR_INVALID_ARG, "plan is NULL");
+    if (range) describe(*p->range.sched, range);
+    if (az) describe(*p->az.sched, az);
+    return SAR_OK;
+}
+
+sar_status sar_autotune(int64_t n, int64_t n_lines, int32_t reps, int32_t kind, sar_stream stream,
+                        sar_schedule_desc *best, float *best_ms, float *all_ms, int32_t all_cap) {
+    sar_status st;
+    if ((st = check_length(n, "n")) != SAR_OK) return st;
+    if (n_lines < 1 || reps < 1) return fail(SAR_ERR_INVALID_ARG, "n_lines and reps must be >= 1");
+    if (kind != SAR_TUNE_FUSED && kind != SAR_TUNE_RANGE_CT) return fail(SAR_ERR_INVALID_ARG, "unknown kind %d", kind);
+    if (kind == SAR_TUNE_RANGE_CT && n_lines % 4)
+        return fail(SAR_ERR_INVALID_ARG, "folded range pass needs n_lines a multiple of 4");
+    const size_t bytes = sizeof(float2) * (size_t)n * (size_t)n_lines;
+    int cands = 0;
+    for (int i = 0; i < sar::schedule_count(); ++i) cands += sar::schedule_at(i)->n == n;
+    if (cands == 0) return fail(SAR_ERR_UNSUPPORTED, "no compiled schedule for n = %lld", (long long)n);
+    float2 *in = nullptr, *outb = nullptr, *tab = nullptr;
+    int max_tw = 0;
+    for (int i = 0; i < sar::schedule_count(); ++i)
+        if (sar::schedule_at(i)->n == n && sar::schedule_at(i)->tw_elems > max_tw) max_tw = sar::schedule_at(i)->tw_elems;
+    if (cudaMalloc(&in, bytes) != cudaSuccess || cudaMalloc(&outb, bytes) != cudaSuccess ||
+        cudaMalloc(&tab, sizeof(float2) * (size_t)(max_tw + n + 32)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(in);
+        cudaFree(outb);
+        cudaFree(tab);
+        return fail(SAR_ERR_OUT_OF_MEMORY, "autotune buffers (2 x %zu bytes)", bytes);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const SchedDesc *win = nullptr;
+    float win_ms = 0.f;
+    cudaError_t e = cudaMemsetAsync(in, 0, bytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tab, 0, sizeof(float2) * (size_t)(max_tw + n + 32), s);
+    const sar::FusedCtl ctl{(int *)(tab + max_tw + n), plan_wait_cycles(), -1};
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    std::vector<float> times;
+    int cand = 0;
+    for (int i = 0; i < sar::schedule_count() && e == cudaSuccess; ++i) {
+        const SchedDesc &d = *sar::schedule_at(i);
+        if (d.n != n) continue;
+        const bool ct = kind == SAR_TUNE_RANGE_CT;
+        if (ct && !d.fused_ct) {
+            if (all_ms && cand < all_cap) all_ms[cand] = 0.f;
+            ++cand;
+            continue;
+        }
+        if ((e = d.prepare()) != cudaSuccess) break;
+        float2 *tw = tab + n, *filt = tab;
+        if ((e = sar::build_twiddles(d, tw, s)) != cudaSuccess) break;
+        auto run = [&]() {
+            return ct ? d.fused_ct(in, outb, n_lines, n, n_lines, filt, tw, s)
+                      : d.fused(in, outb, n_lines, n, (int)n, filt, tw, ctl, s);
+        };
+        // warm-up, then reps timed launches
+        if ((e = run()) != cudaSuccess) break;
+        times.clear();
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+            cudaEventRecord(e0, s);
+            e = run();
+            cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            times.push_back(ms);
+        }
+        if (e != cudaSuccess) break;
+        std::sort(times.begin(), times.end());
+        const float med = times[times.size() / 2];
+        if (all_ms && cand < all_cap) all_ms[cand] = med;
+        ++cand;
+        if (!win || med < win_ms) {
+            win = &d;
+            win_ms = med;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(s);
+    cudaFree(in);
+    cudaFree(outb);
+    cudaFree(tab);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune");
+    if (!win) return fail(SAR_ERR_UNSUPPORTED, "no schedule of n = %lld has that kind of kernel", (long long)n);
+    if (kind == SAR_TUNE_RANGE_CT)
+        sar::set_preferred_ct_schedule(win);
+    else
+        sar::set_preferred_schedule(win);
+    if (best) describe(*win, best);
+    if (best_ms) *best_ms = win_ms;
+    return SAR_OK;
+}
+
 sar_status sar_plan_destroy(sar_plan p) {
     if (!p) return SAR_OK;
     cudaFree(p->block);
@@ -238,10 +412,10 @@ sar_status sar_plan_destroy(sar_plan p) {
     return SAR_OK;
 }
 
-static sar_status run_fused(const LinePlan &lp, int64_t n_lines, const void *in, void *out, cudaStream_t s,
-                            const char *what) {
+static sar_status run_fused(const sar_plan_s *p, const LinePlan &lp, int64_t n_lines, const void *in, void *out,
+                            cudaStream_t s, const char *what) {
     const SchedDesc &d = *lp.sched;
-    cudaError_t e = d.fused((const float2 *)in, (float2 *)out, n_lines, d.n, d.n, lp.filt, lp.tw, s);
+    cudaError_t e = d.fused((const float2 *)in, (float2 *)out, n_lines, d.n, d.n, lp.filt, lp.tw, p->ctl, s);
     if (e != cudaSuccess) return cuda_fail(e, what);
     return SAR_OK;
 }
@@ -250,14 +424,24 @@ sar_status sar_range_compress(sar_plan p, void *data, sar_stream stream) {
     if (!p) return fail(SAR_ERR_INVALID_ARG, "plan is NULL");
     sar_status st = check_device_ptr(data, "data");
     if (st != SAR_OK) return st;
-    return run_fused(p->range, p->n_az, data, data, (cudaStream_t)stream, "range compression launch");
+    return run_fused(p, p->range, p->n_az, data, data, (cudaStream_t)stream, "range compression launch");
 }
 
 sar_status sar_azimuth_compress(sar_plan p, void *data, sar_stream stream) {
     if (!p) return fail(SAR_ERR_INVALID_ARG, "plan is NULL");
     sar_status st = check_device_ptr(data, "data");
     if (st != SAR_OK) return st;
-    return run_fused(p->az, p->n_range, data, data, (cudaStream_t)stream, "azimuth compression launch");
+    return run_fused(p, p->az, p->n_range, data, data, (cudaStream_t)stream, "azimuth compression launch");
+}
+
+// Range compression straight into the corner-turned image, then the
+// azimuth pass in place: two kernels.
+static sar_status run_folded(const sar_plan_s *p, const void *raw, void *image, cudaStream_t s) {
+    const SchedDesc &d = *p->range.sched;
+    cudaError_t e = d.fused_ct((const float2 *)raw, (float2 *)image, p->n_az, p->n_range, p->n_az, p->range.filt,
+                               p->range.tw, s);
+    if (e != cudaSuccess) return cuda_fail(e, "range compression + corner turn launch");
+    return run_fused(p, p->az, p->n_range, image, image, s, "azimuth compression launch");
 }
 
 static bool overlaps(const void *a, const void *b, size_t bytes) {
@@ -285,10 +469,11 @@ sar_status sar_rda_process(sar_plan p, void *raw, void *image, sar_stream stream
     if (overlaps(raw, image, sizeof(float2) * (size_t)(p->n_az * p->n_range)))
         return fail(SAR_ERR_INVALID_ARG, "raw and image overlap");
     cudaStream_t s = (cudaStream_t)stream;
-    if ((st = run_fused(p->range, p->n_az, raw, raw, s, "range compression launch")) != SAR_OK) return st;
+    if (p->fold) return run_folded(p, raw, image, s);
+    if ((st = run_fused(p, p->range, p->n_az, raw, raw, s, "range compression launch")) != SAR_OK) return st;
     cudaError_t e = sar::launch_transpose((const float2 *)raw, (float2 *)image, p->n_az, p->n_range, s);
     if (e != cudaSuccess) return cuda_fail(e, "corner turn launch");
-    return run_fused(p->az, p->n_range, image, image, s, "azimuth compression launch");
+    return run_fused(p, p->az, p->n_range, image, image, s, "azimuth compression launch");
 }
 
 sar_status sar_range_compress_oop(sar_plan p, const void *in, void *out, sar_stream stream) {
@@ -298,7 +483,22 @@ sar_status sar_range_compress_oop(sar_plan p, const void *in, void *out, sar_str
     if ((st = check_device_ptr(out, "out")) != SAR_OK) return st;
     if (in != out && overlaps(in, out, sizeof(float2) * (size_t)(p->n_az * p->n_range)))
         return fail(SAR_ERR_INVALID_ARG, "in and out partially overlap");
-    return run_fused(p->range, p->n_az, in, out, (cudaStream_t)stream, "range compression launch");
+    return run_fused(p, p->range, p->n_az, in, out, (cudaStream_t)stream, "range compression launch");
+}
+
+sar_status sar_range_compress_ct(sar_plan p, const void *raw, void *image, sar_stream stream) {
+    if (!p) return fail(SAR_ERR_INVALID_ARG, "plan is NULL");
+    if (!p->fold) return fail(SAR_ERR_UNSUPPORTED, "this plan does not fold the corner turn into the range pass");
+    sar_status st;
+    if ((st = check_device_ptr(raw, "raw")) != SAR_OK) return st;
+    if ((st = check_device_ptr(image, "image")) != SAR_OK) return st;
+    if (overlaps(raw, image, sizeof(float2) * (size_t)(p->n_az * p->n_range)))
+        return fail(SAR_ERR_INVALID_ARG, "raw and image overlap");
+    const SchedDesc &d = *p->range.sched;
+    cudaError_t e = d.fused_ct((const float2 *)raw, (float2 *)image, p->n_az, p->n_range, p->n_az, p->range.filt,
+                               p->range.tw, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "range compression + corner turn launch");
+    return SAR_OK;
 }
 
 sar_status sar_rda_process_oop(sar_plan p, const void *raw, void *work, void *image, sar_stream stream) {
@@ -311,10 +511,11 @@ sar_status sar_rda_process_oop(sar_plan p, const void *raw, void *work, void *im
     if (overlaps(raw, work, bytes) || overlaps(raw, image, bytes) || overlaps(work, image, bytes))
         return fail(SAR_ERR_INVALID_ARG, "raw, work and image must not overlap");
     cudaStream_t s = (cudaStream_t)stream;
-    if ((st = run_fused(p->range, p->n_az, raw, work, s, "range compression launch")) != SAR_OK) return st;
+    if (p->fold) return run_folded(p, raw, image, s);
+    if ((st = run_fused(p, p->range, p->n_az, raw, work, s, "range compression launch")) != SAR_OK) return st;
     cudaError_t e = sar::launch_transpose((const float2 *)work, (float2 *)image, p->n_az, p->n_range, s);
     if (e != cudaSuccess) return cuda_fail(e, "corner turn launch");
-    return run_fused(p->az, p->n_range, image, image, s, "azimuth compression launch");
+    return run_fused(p, p->az, p->n_range, image, image, s, "azimuth compression launch");
 }
 
 sar_status sar_rda_process_host(sar_plan p, const void *raw, void *image, sar_stream stream) {
@@ -386,6 +587,19 @@ sar_status sar_transpose(int64_t rows, int64_t cols, const void *in, void *out, 
     cudaError_t e = sar::launch_transpose((const float2 *)in, (float2 *)out, rows, cols, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "transpose launch");
     return SAR_OK;
+}
+
+sar_status sar_plan_status(sar_plan p, sar_stream stream) {
+    if (!p) return fail(SAR_ERR_INVALID_ARG, "plan is NULL");
+    int word = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    SAR_CUDA(cudaMemcpyAsync(&word, p->status, sizeof(int), cudaMemcpyDeviceToHost, s), "status read");
+    SAR_CUDA(cudaStreamSynchronize(s), "stream synchronise");
+    if (word == 0) return SAR_OK;
+    SAR_CUDA(cudaMemsetAsync(p->status, 0, sizeof(int), s), "status reset");
+    SAR_CUDA(cudaStreamSynchronize(s), "stream synchronise");
+    return fail(SAR_ERR_TIMEOUT, "a device-side wait of this plan's kernels timed out; the affected lines were "
+                                 "not written");
 }
 
 sar_status sar_sync(sar_stream stream) {

@@ -28,14 +28,15 @@
 
 namespace sar {
 
-template <int N_, int E_, int R1_, int R2_, int R3_ = 1>
+template <int N_, int E_, int R1_, int R2_, int R3_ = 1, int MINB_ = 0>
 struct Sched {
     static constexpr int N = N_, E = E_, T = N_ / E_;
+    static constexpr int MINB = MINB_;   // > 0: registers capped for MINB resident blocks per SM
     static constexpr int R1 = R1_, R2 = R2_, R3 = R3_;
     static constexpr int P = (R3_ > 1) ? 3 : 2;
     static constexpr int S1 = N / R1, S2 = S1 / R2, S3 = (P == 3) ? S2 / R3 : 0;
     static constexpr int RL = (P == 3) ? R3 : R2;                 // radix of the last pass
-    static constexpr int PADSH = (RL == 16) ? 4 : (RL == 32) ? 5 : (RL == 64) ? 6 : (RL == 8) ? 3 : 7;
+    static constexpr int PADSH = (RL == 16) ? 4 : (RL == 32) ? 5 : (RL == 64) ? 6 : (RL == 8) ? 3 : (RL == 4) ? 2 : 7;
     static constexpr int SMEM_ELEMS = N + (N >> PADSH);            // per line
     static constexpr int TW_ELEMS = R1 * S1 + ((P == 3) ? R2 * S2 : 0);  // twiddle table length
     static_assert(R1 * R2 * R3 == N, "radices must multiply to N");
@@ -207,9 +208,8 @@ __device__ __forceinline__ void inverse_passes(float2 (&v)[SC::E], float2* sm, c
 
 // Fused line compression, Sec. II-B: y = IFFT(FFT(x) . H), in place allowed.
 template <class SC, int LPB, bool RAGGED>
-__global__ void __launch_bounds__(SC::T * LPB)
-fused_compress_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld,
-                      int valid, const float2* filt, const float2* tw) {
+__device__ __forceinline__ void fused_compress_body(const float2* in, float2* out, int64_t n_lines, int64_t ld,
+                                                    int valid, const float2* filt, const float2* tw) {
     extern __shared__ float2 smem_dyn[];
     const int lib = threadIdx.x / SC::T;
     const int t = threadIdx.x % SC::T;
@@ -222,6 +222,21 @@ fused_compress_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld
     filter_multiply<SC>(filt, t, v);
     inverse_passes<SC, LPB>(v, sm, tw, t, lib);
     global_store<SC, RAGGED>(out + line * ld, valid, t, v);
+}
+
+// The compiler's own register choice (only the block size is bounded) ...
+template <class SC, int LPB, bool RAGGED>
+__global__ void __launch_bounds__(SC::T * LPB)
+fused_compress_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld, int valid, const float2* filt,
+                      const float2* tw) {
+    fused_compress_body<SC, LPB, RAGGED>(in, out, n_lines, ld, valid, filt, tw);
+}
+// ... or registers capped so that SC::MINB blocks fit on one SM.
+template <class SC, int LPB, bool RAGGED>
+__global__ void __launch_bounds__(SC::T * LPB, SC::MINB)
+fused_compress_kernel_capped(const float2* in, float2* out, int64_t n_lines, int64_t ld, int valid,
+                             const float2* filt, const float2* tw) {
+    fused_compress_body<SC, LPB, RAGGED>(in, out, n_lines, ld, valid, filt, tw);
 }
 
 // Plain forward (or inverse) DFT of each line, natural order in and out,

@@ -1,6 +1,8 @@
 // Schedule lookup and the host-side filter permutation.
 #include <string.h>
 
+#include <mutex>
+
 #include "registry.h"
 
 namespace sar {
@@ -33,11 +35,55 @@ const SchedDesc *find_schedule(const char *name) {
     return nullptr;
 }
 
-// First compiled schedule of each length is its default.
+namespace {
+std::mutex g_pref_mu;
+const SchedDesc *g_preferred[32] = {};      // by log2(n)
+const SchedDesc *g_preferred_ct[32] = {};   // folded range pass, by log2(n)
+int log2i(int n) {
+    int k = 0;
+    while ((1 << k) < n && k < 31) ++k;
+    return k;
+}
+}  // namespace
+
+// The preferred schedule of a length: set by the autotuner or the caller,
+// otherwise the first compiled schedule of that length.
 const SchedDesc *default_schedule(int n) {
+    {
+        std::lock_guard<std::mutex> lk(g_pref_mu);
+        const SchedDesc *p = g_preferred[log2i(n)];
+        if (p && p->n == n) return p;
+    }
     for (int i = 0; i < all().n; ++i)
         if (all().p[i]->n == n) return all().p[i];
     return nullptr;
+}
+
+// The preferred schedule of length n that can fold the corner turn into the
+// range pass: the preferred schedule itself if it can, else the first
+// compiled one that can, else nullptr.
+const SchedDesc *default_ct_schedule(int n) {
+    {
+        std::lock_guard<std::mutex> lk(g_pref_mu);
+        const SchedDesc *q = g_preferred_ct[log2i(n)];
+        if (q && q->n == n) return q;
+    }
+    const SchedDesc *p = default_schedule(n);
+    if (p && p->fused_ct) return p;
+    for (int i = 0; i < all().n; ++i)
+        if (all().p[i]->n == n && all().p[i]->fused_ct) return all().p[i];
+    return nullptr;
+}
+
+void set_preferred_schedule(const SchedDesc *d) {
+    std::lock_guard<std::mutex> lk(g_pref_mu);
+    g_preferred[log2i(d->n)] = d;
+    if (d->fused_ct) g_preferred_ct[log2i(d->n)] = d;
+}
+
+void set_preferred_ct_schedule(const SchedDesc *d) {
+    std::lock_guard<std::mutex> lk(g_pref_mu);
+    if (d->fused_ct) g_preferred_ct[log2i(d->n)] = d;
 }
 
 void filter_slot_to_k(const SchedDesc &d, int32_t *idx) {

@@ -8,11 +8,22 @@
 
 namespace sar {
 
+// Extra arguments of the persistent kernels (ignored by the others).
+struct FusedCtl {
+    int *status;              // device status word: 5 after a timed-out wait, else untouched
+    long long wait_cycles;    // bound of every device-side wait, in SM clocks
+    int64_t skip_line;        // test hook: never start the copy of this line (-1: off)
+};
+
 typedef cudaError_t (*fused_fn)(const float2 *in, float2 *out, int64_t n_lines, int64_t ld, int valid,
-                                const float2 *filt, const float2 *tw, cudaStream_t st);
+                                const float2 *filt, const float2 *tw, const FusedCtl &ctl, cudaStream_t st);
 typedef cudaError_t (*dft_fn)(const float2 *in, float2 *out, int64_t n_lines, int64_t ld, int valid,
                               const float2 *tw, int inverse, cudaStream_t st);
 typedef cudaError_t (*prep_fn)(void);
+// range compression with the corner turn folded into the store: in is
+// [n_lines][n] (row stride ld_in), img is [n][ld_img] receiving img[k][l]
+typedef cudaError_t (*fused_ct_fn)(const float2 *in, float2 *img, int64_t n_lines, int64_t ld_in, int64_t ld_img,
+                                   const float2 *filt, const float2 *tw, cudaStream_t st);
 
 struct SchedDesc {
     const char *name;
@@ -22,9 +33,12 @@ struct SchedDesc {
     int smem_bytes;         // dynamic shared memory per block
     int tw_elems;           // twiddle table length
     int rl;                 // radix of the last pass
+    int persistent;         // 1: resident blocks walk the lines, TMA prefetch of the next line
     fused_fn fused;
     dft_fn dft;
     prep_fn prepare;        // raises the dynamic shared-memory limit where needed
+    fused_ct_fn fused_ct;   // nullptr: no folded corner turn for this schedule
+    int ct_lines;           // lines per block of fused_ct (n_lines must be a multiple)
 };
 
 // All compiled schedules (one table per translation unit).
@@ -32,8 +46,11 @@ const SchedDesc *schedules_small(int *count);   // N = 256 .. 2048
 const SchedDesc *schedules_4096(int *count);
 const SchedDesc *schedules_large(int *count);   // N = 8192, 16384
 
-// The default schedule for length n, or nullptr.
+// The preferred schedule for length n, or nullptr.
 const SchedDesc *default_schedule(int n);
+void set_preferred_schedule(const SchedDesc *d);
+const SchedDesc *default_ct_schedule(int n);
+void set_preferred_ct_schedule(const SchedDesc *d);
 // Schedule by name, or nullptr.
 const SchedDesc *find_schedule(const char *name);
 // Visit every schedule.

@@ -7,11 +7,28 @@ using S256 = Sched<256, 16, 16, 16>;     // 16 threads per line
 using S512 = Sched<512, 32, 16, 32>;     // 16 threads per line
 using S1024 = Sched<1024, 32, 32, 32>;   // one warp per line
 using S2048 = Sched<2048, 64, 32, 64>;   // one warp per line
+using S256b = Sched<256, 16, 16, 16>;
+using S512b = Sched<512, 16, 16, 8, 4>;       // 32 threads per line, three passes
+using S1024b = Sched<1024, 16, 16, 16, 4>;    // 64 threads per line
+using S2048b = Sched<2048, 16, 16, 16, 8>;    // 128 threads per line
 const SchedDesc kTable[] = {
+    make_streamed_desc<S2048b, 1, false, -4>("n2048_e16_r16x16x8_s1"),
     make_desc<S256, 8>("n256_e16_r16x16_l8"),
+    make_desc<S256b, 16>("n256_e16_r16x16_l16"),
     make_desc<S512, 8>("n512_e32_r16x32_l8"),
+    make_desc<S512b, 4>("n512_e16_r16x8x4_l4"),
     make_desc<S1024, 4>("n1024_e32_r32x32_l4"),
+    make_desc<S1024b, 2>("n1024_e16_r16x16x4_l2"),
     make_desc<S2048, 2>("n2048_e64_r32x64_l2"),
+    make_desc<S2048b, 1>("n2048_e16_r16x16x8_l1"),
+    make_streamed_desc<S1024, 4, false, 4>("n1024_e32_r32x32_s4"),
+    make_streamed_desc<S512, 8, false, 4>("n512_e32_r16x32_s8"),
+    make_streamed_desc<S256, 8, false, 4>("n256_e16_r16x16_s8"),
+    make_streamed_desc<S2048b, 2, false>("n2048_e16_r16x16x8_s2"),
+    make_persistent_desc<S2048>("n2048_e64_r32x64_p"),
+    make_persistent_desc<S2048b>("n2048_e16_r16x16x8_p"),
+    make_persistent_desc<S1024>("n1024_e32_r32x32_p"),
+    make_persistent_desc<S1024b>("n1024_e16_r16x16x4_p"),
 };
 }  // namespace
 

@@ -1,0 +1,278 @@
+// Group-streamed variant of the fused line compression.
+//
+// Same arithmetic and the same in-place shared-memory geometry as
+// fused_compress_kernel (line_engine.cuh), but each pass is executed one
+// radix group at a time: load the group's R values (from HBM in the first
+// pass, from shared memory otherwise), transform, twiddle, write them back.
+// Only one group is live in registers, so a thread that owns several groups
+// per pass needs about R complex registers instead of E, and with ROLL the
+// loop over groups is not unrolled, which halves the code a warp streams
+// through the instruction cache.  In the first pass the next group's HBM
+// loads are issued before the current group is transformed, so their latency
+// overlaps the arithmetic.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "line_engine.cuh"
+
+namespace sar {
+
+template <int R, int S>
+__device__ __forceinline__ void grp_smem_load(const float2* sm, int base, int padsh, float2 (&g)[R]) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) g[r] = sm[smem_pos(base + r * S, padsh)];
+}
+template <int R, int S>
+__device__ __forceinline__ void grp_smem_store(float2* sm, int base, int padsh, const float2 (&g)[R]) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) sm[smem_pos(base + r * S, padsh)] = g[r];
+}
+template <int R, int S, bool INV>
+__device__ __forceinline__ void grp_twiddle(const float2* tw, int lo, float2 (&g)[R]) {
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+        const float2 w = tw[r * S + lo];
+        g[r] = INV ? cmulc(g[r], w) : cmul(g[r], w);
+    }
+}
+
+// One middle pass (shared memory in, shared memory out) of radix R, stride S.
+// FWD: DFT then twiddle; inverse: conjugate twiddle then inverse DFT.
+template <class SC, int R, int S, bool INV, bool ROLL>
+__device__ __forceinline__ void streamed_mid_pass(float2* sm, const float2* tw, int t) {
+    constexpr int G = SC::E / R;
+#pragma unroll(ROLL ? 1 : G)
+    for (int s = 0; s < G; ++s) {
+        const int g = t + SC::T * s;
+        const int base = group_base<R, S>(g);
+        float2 x[R];
+        grp_smem_load<R, S>(sm, base, SC::PADSH, x);
+        if (!INV) {
+            dft_reg<R, false>(x);
+            grp_twiddle<R, S, false>(tw, group_lo<R, S>(g), x);
+        } else {
+            grp_twiddle<R, S, true>(tw, group_lo<R, S>(g), x);
+            dft_reg<R, true>(x);
+        }
+        grp_smem_store<R, S>(sm, base, SC::PADSH, x);
+    }
+}
+
+// Everything of the fused line compression except the last inverse pass:
+// pass 1 from HBM, the middle passes, the last forward pass with the filter
+// multiply and the first inverse pass, and the inverse middle passes.  On
+// return the line sits in shared memory ready for the inverse pass 1.
+template <class SC, int LPB, bool ROLL>
+__device__ __forceinline__ void streamed_until_last(const float2* src, float2* sm, const float2* filt,
+                                                    const float2* tw, int t, int lib) {
+    constexpr int R1 = SC::R1, S1 = SC::S1, G1 = SC::E / R1;
+    constexpr int RL = SC::RL, GL = SC::E / RL;
+
+    // ---- forward pass 1: HBM -> DFT -> twiddle -> shared memory, with the
+    //      next group's loads in flight during the current group's arithmetic
+    float2 cur[R1];
+#pragma unroll
+    for (int r = 0; r < R1; ++r) cur[r] = src[t + r * S1];
+#pragma unroll(ROLL ? 1 : G1)
+    for (int s = 0; s < G1; ++s) {
+        const int lo = t + SC::T * s;
+        float2 nxt[R1];
+        if (s + 1 < G1) {
+#pragma unroll
+            for (int r = 0; r < R1; ++r) nxt[r] = src[lo + SC::T + r * S1];
+        }
+        dft_reg<R1, false>(cur);
+        grp_twiddle<R1, S1, false>(tw, lo, cur);
+        grp_smem_store<R1, S1>(sm, lo, SC::PADSH, cur);
+        if (s + 1 < G1) {
+#pragma unroll
+            for (int r = 0; r < R1; ++r) cur[r] = nxt[r];
+        }
+    }
+    line_sync<SC, LPB>(lib);
+    const float2* tw2 = tw + SC::R1 * SC::S1;
+    if constexpr (SC::P == 3) {
+        streamed_mid_pass<SC, SC::R2, SC::S2, false, ROLL>(sm, tw2, t);
+        line_sync<SC, LPB>(lib);
+    }
+    // ---- last forward pass, filter, first inverse pass: one group at a time
+#pragma unroll(ROLL ? 1 : GL)
+    for (int s = 0; s < GL; ++s) {
+        const int g = t + SC::T * s;
+        float2 x[RL];
+        grp_smem_load<RL, 1>(sm, g * RL, SC::PADSH, x);
+        dft_reg<RL, false>(x);
+#pragma unroll
+        for (int r = 0; r < RL; ++r) x[r] = cmul(x[r], filt[(s * RL + r) * SC::T + t]);
+        dft_reg<RL, true>(x);
+        grp_smem_store<RL, 1>(sm, g * RL, SC::PADSH, x);
+    }
+    line_sync<SC, LPB>(lib);
+    if constexpr (SC::P == 3) {
+        streamed_mid_pass<SC, SC::R2, SC::S2, true, ROLL>(sm, tw2, t);
+        line_sync<SC, LPB>(lib);
+    }
+}
+
+template <class SC, int LPB, bool ROLL>
+__device__ __forceinline__ void fused_streamed_body(const float2* in, float2* out, int64_t n_lines, int64_t ld,
+                                                    const float2* filt, const float2* tw) {
+    extern __shared__ float2 smem_dyn[];
+    const int lib = threadIdx.x / SC::T;
+    const int t = threadIdx.x % SC::T;
+    const int64_t line = (int64_t)blockIdx.x * LPB + lib;
+    if (line >= n_lines) return;
+    float2* sm = smem_dyn + lib * SC::SMEM_ELEMS;
+    float2* dst = out + line * ld;
+    constexpr int R1 = SC::R1, S1 = SC::S1, G1 = SC::E / R1;
+    streamed_until_last<SC, LPB, ROLL>(in + line * ld, sm, filt, tw, t, lib);
+    // ---- inverse pass 1: shared memory -> twiddle -> inverse DFT -> HBM
+#pragma unroll(ROLL ? 1 : G1)
+    for (int s = 0; s < G1; ++s) {
+        const int lo = t + SC::T * s;
+        float2 x[R1];
+        grp_smem_load<R1, S1>(sm, lo, SC::PADSH, x);
+        grp_twiddle<R1, S1, true>(tw, lo, x);
+        dft_reg<R1, true>(x);
+#pragma unroll
+        for (int r = 0; r < R1; ++r) dst[lo + r * S1] = x[r];
+    }
+}
+
+// Range compression with the corner turn folded into its store (the
+// paper's Sec. IV-A steps 1 and 2 in one kernel).  A block compresses QL
+// consecutive range lines a0 .. a0+QL-1 (QL = 4); after the inverse pass the
+// lines are parked in shared memory in natural order and written out
+// transposed: range bin n of the QL lines is one QL*8-byte chunk (with QL = 4
+// a full 32-byte HBM sector) of image row n, image[n][a0 .. a0+QL-1].  The separate transpose
+// kernel and its 16 bytes per sample of HBM traffic disappear.
+// Requires n_lines % QL == 0 and 16-byte aligned rows of the image.
+template <class SC, int QL, bool ROLL>
+__device__ __forceinline__ void fused_range_ct_body(const float2* in, float2* img, int64_t n_lines, int64_t ld_in,
+                                                    int64_t ld_img, const float2* filt, const float2* tw) {
+    extern __shared__ float2 smem_dyn[];
+    const int lib = threadIdx.x / SC::T;
+    const int t = threadIdx.x % SC::T;
+    const int64_t a0 = (int64_t)blockIdx.x * QL;
+    const int64_t line = a0 + lib;
+    float2* sm = smem_dyn + lib * SC::SMEM_ELEMS;
+    constexpr int R1 = SC::R1, S1 = SC::S1, G1 = SC::E / R1;
+    streamed_until_last<SC, QL, ROLL>(in + line * ld_in, sm, filt, tw, t, lib);
+    // ---- inverse pass 1 into registers, then natural order into shared memory
+    float2 v[SC::E];
+#pragma unroll
+    for (int s = 0; s < G1; ++s) {
+        const int lo = t + SC::T * s;
+        float2 x[R1];
+        grp_smem_load<R1, S1>(sm, lo, SC::PADSH, x);
+        grp_twiddle<R1, S1, true>(tw, lo, x);
+        dft_reg<R1, true>(x);
+#pragma unroll
+        for (int r = 0; r < R1; ++r) v[s * R1 + r] = x[r];
+    }
+    line_sync<SC, QL>(lib);
+#pragma unroll
+    for (int s = 0; s < G1; ++s) {
+        const int lo = t + SC::T * s;
+#pragma unroll
+        for (int r = 0; r < R1; ++r) sm[lo + r * S1] = v[s * R1 + r];
+    }
+    __syncthreads();
+    // ---- transposed store: one QL*8-byte chunk per range bin
+    static_assert(QL == 2 || QL == 4, "chunks of two or four complex64");
+    for (int n = threadIdx.x; n < SC::N; n += SC::T * QL) {
+        float4* dst = reinterpret_cast<float4*>(img + (int64_t)n * ld_img + a0);
+        const float2 c0 = smem_dyn[n], c1 = smem_dyn[SC::SMEM_ELEMS + n];
+        dst[0] = make_float4(c0.x, c0.y, c1.x, c1.y);
+        if constexpr (QL == 4) {
+            const float2 c2 = smem_dyn[2 * SC::SMEM_ELEMS + n], c3 = smem_dyn[3 * SC::SMEM_ELEMS + n];
+            dst[1] = make_float4(c2.x, c2.y, c3.x, c3.y);
+        }
+    }
+}
+
+// The same fold with one line per block and QC blocks per thread-block
+// cluster (QC = 4, 8 or 16): each block compresses its own line and parks it,
+// in natural order, in its shared memory; after a cluster barrier block k of
+// the cluster gathers range bins [k N/QC, (k+1) N/QC) of all QC lines through
+// distributed shared memory and writes each bin's QC samples as one
+// QC*8-byte chunk of image row n (with QC = 16 a full 128-byte line, written
+// by eight lanes of 16 bytes).  A block needs one line of shared memory, not
+// QC, so an SM keeps as many lines in flight as the unfolded kernel.  A second
+// cluster barrier keeps every block's shared memory alive until its
+// neighbours have read it.  Launched with a cluster dimension of QC.
+template <class SC, int QC, bool ROLL>
+__device__ __forceinline__ void fused_range_ct_cluster_body(const float2* in, float2* img, int64_t ld_in,
+                                                            int64_t ld_img, const float2* filt,
+                                                            const float2* tw) {
+    namespace cg = cooperative_groups;
+    extern __shared__ float2 smem_dyn[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int t = threadIdx.x;
+    const int rank = (int)cluster.block_rank();
+    const int64_t line = blockIdx.x;
+    const int64_t a0 = line - rank;
+    float2* sm = smem_dyn;
+    constexpr int R1 = SC::R1, S1 = SC::S1, G1 = SC::E / R1;
+    streamed_until_last<SC, 1, ROLL>(in + line * ld_in, sm, filt, tw, t, 0);
+    float2 v[SC::E];
+#pragma unroll
+    for (int s = 0; s < G1; ++s) {
+        const int lo = t + SC::T * s;
+        float2 x[R1];
+        grp_smem_load<R1, S1>(sm, lo, SC::PADSH, x);
+        grp_twiddle<R1, S1, true>(tw, lo, x);
+        dft_reg<R1, true>(x);
+#pragma unroll
+        for (int r = 0; r < R1; ++r) v[s * R1 + r] = x[r];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < G1; ++s) {
+        const int lo = t + SC::T * s;
+#pragma unroll
+        for (int r = 0; r < R1; ++r) sm[lo + r * S1] = v[s * R1 + r];
+    }
+    cluster.sync();
+    constexpr int NQ = SC::N / QC;       // range bins gathered by this block
+    constexpr int LPN = QC / 2;          // lanes per bin, 16 bytes (two lines) each
+    for (int idx = t; idx < NQ * LPN; idx += SC::T) {
+        const int n = rank * NQ + idx / LPN;
+        const int p = idx % LPN;
+        const float2 c0 = cluster.map_shared_rank(sm, 2 * p)[n];
+        const float2 c1 = cluster.map_shared_rank(sm, 2 * p + 1)[n];
+        *reinterpret_cast<float4*>(img + (int64_t)n * ld_img + a0 + 2 * p) = make_float4(c0.x, c0.y, c1.x, c1.y);
+    }
+    cluster.sync();
+}
+
+template <class SC, int QC, bool ROLL>
+__global__ void __launch_bounds__(SC::T)
+fused_range_ct_cluster_kernel(const float2* in, float2* img, int64_t ld_in, int64_t ld_img, const float2* filt,
+                              const float2* tw) {
+    fused_range_ct_cluster_body<SC, QC, ROLL>(in, img, ld_in, ld_img, filt, tw);
+}
+
+template <class SC, int QL, bool ROLL>
+__global__ void __launch_bounds__(SC::T * QL)
+fused_range_ct_kernel(const float2* in, float2* img, int64_t n_lines, int64_t ld_in, int64_t ld_img,
+                      const float2* filt, const float2* tw) {
+    fused_range_ct_body<SC, QL, ROLL>(in, img, n_lines, ld_in, ld_img, filt, tw);
+}
+
+template <class SC, int LPB, bool ROLL>
+__global__ void __launch_bounds__(SC::T * LPB)
+fused_streamed_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld, const float2* filt,
+                      const float2* tw) {
+    fused_streamed_body<SC, LPB, ROLL>(in, out, n_lines, ld, filt, tw);
+}
+// registers capped so that SC::MINB blocks fit on one SM
+template <class SC, int LPB, bool ROLL>
+__global__ void __launch_bounds__(SC::T * LPB, SC::MINB)
+fused_streamed_kernel_capped(const float2* in, float2* out, int64_t n_lines, int64_t ld, const float2* filt,
+                             const float2* tw) {
+    fused_streamed_body<SC, LPB, ROLL>(in, out, n_lines, ld, filt, tw);
+}
+
+}  // namespace sar

@@ -43,5 +43,10 @@ def rda_bytes(n_az: int, n_range: int) -> int:
     return fused_pass_bytes(n_az, n_range) + corner_turn_bytes(n_az, n_range) + fused_pass_bytes(n_range, n_az)
 
 
+def rda_bytes_folded(n_az: int, n_range: int) -> int:
+    """Corner turn folded into the range pass: 32 bytes per sample."""
+    return fused_pass_bytes(n_az, n_range) + fused_pass_bytes(n_range, n_az)
+
+
 def rda_flops(n_az: int, n_range: int) -> float:
     return n_az * fused_line_flops(n_range) + n_range * fused_line_flops(n_az)

@@ -46,7 +46,7 @@ def test_argument_errors_without_gpu(sar):
     assert lib.sar_plan_create(256, 32768, ctypes.byref(f), ctypes.byref(h)) == sar.SAR_ERR_UNSUPPORTED
     assert lib.sar_plan_create(0, 256, ctypes.byref(f), ctypes.byref(h)) == sar.SAR_ERR_INVALID_ARG
     assert "n_range" in sar.sar_last_error()
-    f2 = sar.sar_filters(None, None, 0, 1)
+    f2 = sar.sar_filters(None, None, 0, 2)
     assert lib.sar_plan_create(256, 256, ctypes.byref(f2), ctypes.byref(h)) == sar.SAR_ERR_INVALID_ARG
     f3 = sar.sar_filters(None, None, 7, 0)
     assert lib.sar_plan_create(256, 256, ctypes.byref(f3), ctypes.byref(h)) == sar.SAR_ERR_UNSUPPORTED

@@ -132,6 +132,147 @@ def test_azimuth_compress_vs_oracle(sar, orc, n):
     plan.destroy()
 
 
+def _all_schedules():
+    import ctypes
+    import importlib
+    try:
+        sar = importlib.import_module("paper_2604_03585_gb300")
+    except ImportError:
+        return []
+    return [sar.sar_schedule_get(i)["name"] for i in range(sar.sar_schedule_count())]
+
+
+@pytest.mark.parametrize("name", _all_schedules() or ["n4096_e64_r64x64_l1"])
+def test_every_schedule_vs_oracle(sar, orc, name):
+    d = [x for x in sar.schedules() if x["name"] == name][0]
+    n, n_az = d["n"], 256
+    Hr = rand_c64(n, seed=77 + n)
+    Ha = rand_c64(n_az, seed=78)
+    plan = sar.sar_plan_create_ex(n, n_az, dev(Hr), dev(Ha), range_schedule=name)
+    assert sar.sar_plan_get_schedules(plan)[0]["name"] == name
+    n_lines = n_az
+    x = rand_c64(n_lines * n, seed=79 + n).reshape(n_lines, n)
+    xd = dev(x)
+    sar.sar_range_compress(plan, xd)
+    got = host(xd)
+    ref = orc.compress_lines(x, Hr.astype(np.complex128), nthreads=NTHREADS)
+    assert M.rel_l2(got, ref) < 4e-6
+    plan.destroy()
+
+
+def _persistent_schedules():
+    return [n for n in _all_schedules() if n.endswith("_p")]
+
+
+@pytest.mark.parametrize("name", _persistent_schedules() or ["n4096_e32_r16x16x16_p"])
+def test_persistent_many_lines_per_block(sar, orc, name):
+    """More lines than resident blocks: every block loops, double-buffering
+    its TMA copies; in place and out of place."""
+    d = [x for x in sar.schedules() if x["name"] == name][0]
+    n = d["n"]
+    n_lines = 4096 if n <= 4096 else 2048
+    Hr = rand_c64(n, seed=91 + n)
+    Ha = rand_c64(n_lines, seed=92)
+    plan = sar.sar_plan_create_ex(n, n_lines, dev(Hr), dev(Ha), range_schedule=name)
+    x = rand_c64(n_lines * n, seed=93 + n).reshape(n_lines, n)
+    xd = dev(x)
+    out = empty_c64(n_lines, n)
+    sar.sar_range_compress_oop(plan, xd, out)
+    sar.sar_range_compress(plan, xd)
+    sar.sar_plan_status(plan)
+    got = host(out)
+    assert np.array_equal(host(xd), got)
+    ref = orc.compress_lines(x, Hr.astype(np.complex128), nthreads=NTHREADS)
+    assert M.rel_l2(got, ref) < 4e-6
+    plan.destroy()
+
+
+def test_persistent_wait_timeout_is_reported(sar):
+    """A copy that is never started (host-side injection) makes the bounded
+    device wait run out: the plan reports SAR_ERR_TIMEOUT, the context stays
+    usable and the next plan computes normally."""
+    n, n_lines = 4096, 1024
+    name = "n4096_e32_r16x16x16_p"
+    Hr, Ha = rand_c64(n, 1), rand_c64(n_lines, 2)
+    os.environ["SAR_FAULT_INJECT_SKIP_LINE"] = "700"
+    os.environ["SAR_WAIT_CYCLES"] = "2000000"          # about a millisecond
+    try:
+        plan = sar.sar_plan_create_ex(n, n_lines, dev(Hr), dev(Ha), range_schedule=name)
+    finally:
+        del os.environ["SAR_FAULT_INJECT_SKIP_LINE"]
+        del os.environ["SAR_WAIT_CYCLES"]
+    x = dev(rand_c64(n_lines * n, seed=5).reshape(n_lines, n))
+    sar.sar_range_compress(plan, x)
+    with pytest.raises(sar.SarError) as e:
+        sar.sar_plan_status(plan)
+    assert e.value.status == sar.SAR_ERR_TIMEOUT
+    sar.sar_plan_status(plan)                           # the record was cleared
+    plan.destroy()
+    plan = sar.sar_plan_create_ex(n, n_lines, dev(Hr), dev(Ha), range_schedule=name)
+    y = empty_c64(n_lines, n)
+    sar.sar_range_compress_oop(plan, x, y)
+    sar.sar_plan_status(plan)
+    sar.sar_sync()
+    plan.destroy()
+
+
+def _ct_schedules():
+    try:
+        import paper_2604_03585_gb300 as sar
+    except ImportError:
+        return []
+    out = []
+    for name in _all_schedules():
+        d = [x for x in sar.schedules() if x["name"] == name][0]
+        out.append(name)
+    return out
+
+
+@pytest.mark.parametrize("name", [n for n in _all_schedules()] or ["n4096_e32_r16x16x16_sr1"])
+def test_folded_corner_turn_matches_unfolded(sar, orc, name):
+    """sar_rda_process with the corner turn folded into the range pass gives
+    bit-for-bit the result of the three separate kernels (same schedule), and
+    both match the oracle; raw is left untouched by the folded path."""
+    d = [x for x in sar.schedules() if x["name"] == name][0]
+    n_range = d["n"]
+    n_az = 256
+    Hr, Ha = rand_c64(n_range, seed=5 + n_range), rand_c64(n_az, seed=6)
+    raw = rand_c64(n_az * n_range, seed=7 + n_range).reshape(n_az, n_range)
+    folded = sar.sar_plan_create_ex(n_range, n_az, dev(Hr), dev(Ha), range_schedule=name)
+    if not sar.sar_plan_folds_corner_turn(folded):
+        folded.destroy()
+        pytest.skip("schedule has no folded corner turn")
+    plain = sar.sar_plan_create_ex(n_range, n_az, dev(Hr), dev(Ha), range_schedule=name,
+                                   flags=sar.SAR_PLAN_UNFOLDED_CORNER_TURN)
+    assert not sar.sar_plan_folds_corner_turn(plain)
+    r1, r2 = dev(raw), dev(raw)
+    i1, i2 = empty_c64(n_range, n_az), empty_c64(n_range, n_az)
+    sar.sar_rda_process(folded, r1, i1)
+    sar.sar_rda_process(plain, r2, i2)
+    a, b = host(i1), host(i2)
+    assert np.array_equal(a, b)
+    assert np.array_equal(host(r1), raw)
+    ref = orc.rda(raw, Hr.astype(np.complex128), Ha.astype(np.complex128), nthreads=NTHREADS)
+    assert M.rel_l2(a, ref) < 1e-5
+    folded.destroy()
+    plain.destroy()
+
+
+def test_autotune_picks_a_valid_schedule(sar):
+    best, ms, allt = sar.sar_autotune(1024, 2048, reps=3)
+    assert best["n"] == 1024 and ms > 0
+    assert set(allt) == {d["name"] for d in sar.schedules(1024)}
+    assert min(allt.values()) == pytest.approx(ms)
+    best_ct, ms_ct, all_ct = sar.sar_autotune(4096, 256, reps=2, kind=sar.SAR_TUNE_RANGE_CT)
+    assert best_ct["name"] in all_ct and ms_ct == pytest.approx(min(all_ct.values()))
+    plan = sar.sar_plan_create(4096, 256, empty_c64(4096), empty_c64(256))
+    assert sar.sar_plan_folds_corner_turn(plan)
+    assert sar.sar_plan_get_schedules(plan)[0]["name"] == best_ct["name"]
+    plan.destroy()
+    with pytest.raises(sar.SarError):
+        sar.sar_plan_create_ex(1024, 256, empty_c64(1024), empty_c64(256), range_schedule="n4096_e64_r64x64_l1")
+
+
 # ---------------------------------------------------------------------------
 # the corner turn: bit-exact
 # ---------------------------------------------------------------------------
