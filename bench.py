@@ -323,6 +323,15 @@ def main():
     bytes_pass = roofline.fused_pass_bytes(N_AZ, N_RANGE)
     dominant = max(kern_ms, key=kern_ms.get)
     dom_ms = kern_ms[dominant]
+    if dominant == "range_pass+corner_turn":
+        traffic_key = "range_ct " + sched_r["name"]
+    elif dominant == "range_pass":
+        traffic_key = "fused " + sched_r["name"]
+    elif dominant == "azimuth_pass":
+        traffic_key = "fused " + sched_a["name"]
+    else:
+        traffic_key = None
+    traffic = roofline.recorded_traffic(traffic_key, os.path.join(ROOT, "profiles")) if traffic_key else None
     achieved = bytes_pass / (dom_ms * 1e-3) / 1e9
     path_bytes = roofline.rda_bytes(N_AZ, N_RANGE)            # three passes, 48 B/sample
     path_gbs = path_bytes / (ms_step * 1e-3) / 1e9
@@ -351,8 +360,10 @@ def main():
                    "l2": "inputs larger than L2: 4 rotating 128 MiB raw buffers, 384 MiB touched per step",
                    "range_schedule": sched_r["name"], "azimuth_schedule": sched_a["name"]},
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
-                     "bytes_per_launch": bytes_pass},
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+                     "bytes_per_launch": bytes_pass,
+                     "traffic_note": "ncu dram read+write per launch (profiles/ncu_traffic.json); writes still in "
+                                     "L2 when the kernel ends are not counted"},
         "path_roofline": {"bytes_per_step": path_bytes, "achieved": path_gbs, "peak": peak, "unit": "GB/s",
                           "frac": path_gbs / peak, "bytes_note": "three passes at 16 B/sample each"},
         "path_roofline_folded": {"bytes_per_step": min_bytes,

@@ -13,9 +13,14 @@ Pure host arithmetic; importing this module needs neither torch nor a GPU.
 """
 from __future__ import annotations
 
+import glob
+import hashlib
+import json
 import math
+import os
 
 C64 = 8  # bytes per complex64 sample
+_HERE = os.path.dirname(os.path.abspath(__file__))
 
 
 def fft_flops(n: int) -> float:
@@ -50,3 +55,32 @@ def rda_bytes_folded(n_az: int, n_range: int) -> int:
 
 def rda_flops(n_az: int, n_range: int) -> float:
     return n_az * fused_line_flops(n_range) + n_range * fused_line_flops(n_az)
+
+
+def kernel_source_hash() -> str:
+    """sha256 over the CUDA sources of the kernels (headers and schedule
+    tables); a recorded ncu traffic figure is valid only for this hash."""
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(_HERE, "csrc", "*.cuh")) +
+                   glob.glob(os.path.join(_HERE, "csrc", "sched_*.cu")) +
+                   glob.glob(os.path.join(_HERE, "csrc", "corner_turn.cu")))
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(key: str, profiles_dir: str) -> int | None:
+    """DRAM bytes per launch recorded by ncu for `key` ("fused <schedule>" or
+    "range_ct <schedule>"), or None if absent or recorded for other kernel
+    sources."""
+    try:
+        with open(os.path.join(profiles_dir, "ncu_traffic.json")) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_hash") != kernel_source_hash():
+        return None
+    ent = rec.get("kernels", {}).get(key)
+    return int(ent["bytes"]) if ent else None
