@@ -119,15 +119,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def dist_setup(n_gpus: int):
+def dist_setup(init: bool = True):
+    """Rank, world size and local rank from the torchrun environment; with
+    more than one rank, join the process group (NCCL, or gloo when
+    BENCH_BACKEND=gloo).  Replicas only: the group carries the start barrier
+    and the max-over-ranks of the timings, never scene data."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
+    if world > 1 and init:
         import torch.distributed as dist
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        dist.init_process_group("nccl" if os.environ.get("BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+        dist.init_process_group(backend())
     return rank, world, local
+
+
+def backend() -> str:
+    return "gloo" if os.environ.get("BENCH_BACKEND", "nccl") == "gloo" else "nccl"
 
 
 def barrier(world):
@@ -141,9 +149,15 @@ def allmax(x: float, world: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if backend() == "nccl" else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(ms_step_max: float, world: int) -> float:
+    """Whole-job time per scene: every rank finishes one scene per step, so
+    `world` scenes complete every (max over ranks) step time."""
+    return ms_step_max / world
 
 
 # ---------------------------------------------------------------------------
@@ -217,11 +231,12 @@ def reference_arm(args, rank, world):
 
 def main():
     args = parse()
-    rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
+        # the oracle runs on the host of rank 0 only; other ranks exit at once
+        rank, world, _ = dist_setup(init=False)
         reference_arm(args, rank, world)
-        barrier(world)
         return
+    rank, world, local = dist_setup()
     assert args.warmup >= 3, "at least 3 warm-up steps"
     import numpy as np
     import torch
@@ -351,7 +366,7 @@ def main():
                "sample": f"{lines} range + {lines} azimuth lines of the 4096x4096 scene (FP64 C oracle, "
                          f"{nth} threads), scaled x{N_AZ // lines} to one scene"}
 
-    value = ms_step / world     # whole-job time per scene: world scenes finish every ms_step
+    value = job_value(ms_step, world)
     out = {
         "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
