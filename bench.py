@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--range-schedule", default=None, help="schedule of the range pass (default: autotuned)")
     ap.add_argument("--azimuth-schedule", default=None, help="schedule of the azimuth pass (default: autotuned)")
     ap.add_argument("--no-autotune", action="store_true", help="use the compiled-in preferred schedules")
+    ap.add_argument("--no-extras", action="store_true", help="skip the ragged-batch and serving measurements")
     return ap.parse_args()
 
 
@@ -226,6 +227,111 @@ def reference_arm(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
+# ragged batch: 64 strips of mixed sizes in one CUDA-graph launch
+# ---------------------------------------------------------------------------
+
+def ragged_batch_bench(sar, roofline, dev, stream, peak, reps: int = 10) -> dict:
+    import torch
+    import sarsim
+    specs = sarsim.ragged_batch_specs(4, 64)
+    hr, ha, strips, keep = {}, {}, [], []
+    with torch.cuda.stream(stream):
+        for sp in specs:
+            if sp.n_range not in hr:
+                hr[sp.n_range] = torch.empty(sp.n_range, dtype=torch.complex64, device=dev)
+                sar.sar_make_lfm_spectrum(sp.n_range, *sp.range_chirp, hr[sp.n_range], stream)
+            if sp.l_az not in ha:
+                ha[sp.l_az] = torch.empty(sp.l_az, dtype=torch.complex64, device=dev)
+                sar.sar_make_lfm_spectrum(sp.l_az, *sp.az_chirp, ha[sp.l_az], stream)
+            raw = torch.empty((sp.n_az, sp.n_range), dtype=torch.complex64, device=dev)
+            sar.sar_simulate_echo(sp.n_az, sp.n_range, sp.targets, sp.range_chirp, sp.az_chirp, sp.snr_db, sp.seed,
+                                  raw, stream)
+            img = torch.empty((sp.n_range, sp.n_az), dtype=torch.complex64, device=dev)
+            strips.append(dict(n_range=sp.n_range, n_az=sp.n_az, raw=raw, image=img, range_spectrum=hr[sp.n_range],
+                               az_spectrum=ha[sp.l_az]))
+            keep.append((raw, img))
+    torch.cuda.synchronize()
+    batch = sar.sar_batch_create(strips)
+    info = sar.sar_batch_info(batch)
+    for _ in range(2):
+        sar.sar_batch_run(batch, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    for _ in range(reps):
+        e0.record(stream)
+        sar.sar_batch_run(batch, stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    times.sort()
+    ms = times[len(times) // 2]
+    alg = sum(roofline.rda_bytes(sp.n_az, sp.n_range) for sp in specs)
+    batch.destroy()
+    gbs = alg / (ms * 1e-3) / 1e9
+    return {"strips": info["strips"], "samples": info["samples"], "ms_per_graph_launch": ms,
+            "kernels_per_graph": info["kernels_per_run"], "range_classes": info["range_classes"],
+            "azimuth_classes": info["azimuth_classes"], "algorithmic_bytes": alg,
+            "achieved_GBps": gbs, "frac_of_hbm_peak": gbs / peak,
+            "bytes_note": "48 B per unpadded sample (range pass, corner turn, azimuth pass)",
+            "inputs": "64 seeded strips (sarsim.ragged_batch_specs(4, 64)), echoes by the device simulator"}
+
+
+# ---------------------------------------------------------------------------
+# serving: Poisson stream of mixed-size scenes through the request loop
+# ---------------------------------------------------------------------------
+
+def serving_bench(sar, dev, stream, n_requests: int = 2000, budget_gib: int = 120, max_inflight: int = 32) -> dict:
+    import numpy as np
+    import torch
+    import sarsim
+    variants = 2
+    classes = []
+    with torch.cuda.stream(stream):
+        for size in sarsim.SERVING_SIZES:
+            for v in range(variants):
+                sp = sarsim.serving_scene(size, v)
+                pool = torch.empty((size, size), dtype=torch.complex64, device=dev)
+                sar.sar_simulate_echo(size, size, sp.targets, sp.range_chirp, sp.az_chirp, sp.snr_db, sp.seed, pool,
+                                      stream)
+                hr = torch.empty(size, dtype=torch.complex64, device=dev)
+                ha = torch.empty(size, dtype=torch.complex64, device=dev)
+                sar.sar_make_lfm_spectrum(size, *sp.range_chirp, hr, stream)
+                sar.sar_make_lfm_spectrum(size, *sp.az_chirp, ha, stream)
+                classes.append(dict(n_range=size, n_az=size, pool=pool, range_spectrum=hr, az_spectrum=ha))
+    torch.cuda.synchronize()
+    srv = sar.sar_server_create(classes, hbm_budget_bytes=budget_gib << 30, max_inflight=max_inflight)
+    draws = sarsim.serving_requests(5, n_requests, variants)
+    cls = [k * variants + v for k, v in draws]
+    sar.sar_server_run(srv, [(0.0, c) for c in cls[:64]], mode=sar.SAR_SERVE_CLOSED_LOOP)     # warm-up
+    res = sar.sar_server_run(srv, [(0.0, c) for c in cls], mode=sar.SAR_SERVE_CLOSED_LOOP)
+    makespan = max(r["done_s"] for r in res)
+    sat = n_requests / makespan
+    mean_bytes = float(np.mean([classes[c]["n_range"] * classes[c]["n_az"] * 8 for c in cls]))
+    out = {"requests": n_requests, "size_mix": dict(zip([f"{n}^2" for n in sarsim.SERVING_SIZES],
+                                                        sarsim.SERVING_MIX)),
+           "hbm_budget_GiB": budget_gib, "max_inflight": max_inflight, "mean_scene_MiB": mean_bytes / 2 ** 20,
+           "saturation_scenes_per_s": sat,
+           "saturation_latency_ms": {"p50": float(np.percentile([r["latency_s"] for r in res], 50) * 1e3),
+                                     "p99": float(np.percentile([r["latency_s"] for r in res], 99) * 1e3)}}
+    for load in (0.5, 0.9):
+        arrivals = sarsim.poisson_arrivals(5 + int(load * 10), n_requests, load * sat)
+        res = sar.sar_server_run(srv, [(float(t), c) for t, c in zip(arrivals, cls)], mode=sar.SAR_SERVE_OPEN_LOOP)
+        if any(r["status"] != 0 for r in res):
+            raise RuntimeError("a served request failed")
+        lat = np.array([r["latency_s"] for r in res]) * 1e3
+        span = max(r["done_s"] for r in res) - float(arrivals[0])
+        out[f"load_{int(load * 100)}pct"] = {"offered_scenes_per_s": load * sat, "achieved_scenes_per_s": n_requests / span,
+                                            "p50_ms": float(np.percentile(lat, 50)),
+                                            "p99_ms": float(np.percentile(lat, 99)),
+                                            "mean_ms": float(lat.mean()), "max_ms": float(lat.max())}
+    srv.destroy()
+    out["inputs"] = ("pool scenes by the device simulator (sarsim.serving_scene, 2 variants per size), "
+                     "requests sarsim.serving_requests(5, n), Poisson arrivals sarsim.poisson_arrivals")
+    return out
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 
@@ -366,6 +472,11 @@ def main():
                "sample": f"{lines} range + {lines} azimuth lines of the 4096x4096 scene (FP64 C oracle, "
                          f"{nth} threads), scaled x{N_AZ // lines} to one scene"}
 
+    extras = {}
+    if not args.no_extras:
+        extras["ragged_batch"] = ragged_batch_bench(sar, roofline, dev, stream, peak)
+        extras["serving"] = serving_bench(sar, dev, stream)
+
     value = job_value(ms_step, world)
     out = {
         "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -392,6 +503,7 @@ def main():
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": raw_h.numel() * 8,
                 "d2h_bytes_per_step": img_h.numel() * 8, "api": "sar_rda_process_host, pinned host buffers"},
         "gpu_launches": (2 if folded else 3) * K,
+        **extras,
         "clocks": clk,
     }
     if rank == 0:

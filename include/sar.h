@@ -160,6 +160,21 @@ SAR_API sar_status sar_rda_process_host(sar_plan plan, const void *raw, void *im
  * 1 <= n_chirp <= n; tbp > 0. */
 SAR_API sar_status sar_make_lfm_spectrum(int64_t n, int64_t n_chirp, double tbp, void *out, sar_stream stream);
 
+/* Point-target echo simulator (the chirp signal model of Sec. V-A with
+ * normalised parameters): writes the n_az x n_range complex64 echo of
+ * n_targets unit targets at (targets[2k], targets[2k+1]) = (a0, r0), each
+ * the product of an azimuth chirp (nc_az samples, time-bandwidth tbp_az) and a
+ * range chirp (nc_range, tbp_range) centred on the target (indices modulo the
+ * scene size), plus circular complex Gaussian noise of total variance
+ * 10^(-snr_db/10) drawn from seed (snr_db = NaN: no noise).  Uses the
+ * counter-based splitmix64 / Box-Muller definition of the host generator
+ * `sarsim`, so the two agree to the last bit of complex64 up to FP64
+ * rounding of log/cos/sin.  targets: host array; out: device
+ * complex64[n_az][n_range].  1 <= nc <= n; at most 32 targets. */
+SAR_API sar_status sar_simulate_echo(int64_t n_az, int64_t n_range, const int64_t *targets, int32_t n_targets,
+                                     int64_t nc_range, double tbp_range, int64_t nc_az, double tbp_az,
+                                     double snr_db, uint64_t seed, void *out, sar_stream stream);
+
 /* Unnormalised DFT of n_lines lines of length n (natural order in and out):
  * out[l][k] = sum_j in[l][j] exp(-+2 pi i j k / n), '+' when inverse != 0
  * (computed as conj(FFT(conj x)), Sec. II-C).  in and out: device
@@ -188,6 +203,109 @@ SAR_API sar_status sar_fft_lines_static(int64_t n, int64_t n_lines, const void *
 /* Generic corner turn of a rows x cols complex64 matrix (any sizes >= 1):
  * out[c][r] = in[r][c].  Device pointers, non-overlapping. */
 SAR_API sar_status sar_transpose(int64_t rows, int64_t cols, const void *in, void *out, sar_stream stream);
+
+/* ---- ragged batches ----------------------------------------------------
+ * Many strips of different sizes compressed by one CUDA-graph launch.  A
+ * strip is a raw echo of n_az azimuth lines by n_range range samples; its
+ * azimuth lines are transformed at length L = max(256, next power of two
+ * >= n_az), zero-padded, and the image keeps n_az columns (the correlation
+ * of the zero-padded lines is circular at length L).  The paper processes one
+ * scene size (Sec. IV); batching strips of mixed sizes is this library's
+ * extension of the same three steps. */
+typedef struct {
+    int64_t n_range;            /* power of two in [256, 16384] */
+    int64_t n_az;               /* 1 ... 16384 azimuth lines (L <= 16384) */
+    const void *raw;            /* device complex64[n_az][n_range], read only */
+    void *image;                /* device complex64[n_range][n_az], output */
+    const void *range_spectrum; /* device complex64[n_range] */
+    const void *az_spectrum;    /* device complex64[L] */
+} sar_strip;
+
+typedef struct sar_batch_s *sar_batch;
+
+typedef struct {
+    int64_t strips;          /* strips in the batch */
+    int64_t samples;         /* sum of n_az * n_range */
+    int64_t work_bytes;      /* batch-owned scratch (range-compressed strips) */
+    int32_t kernels_per_run; /* kernels in the graph */
+    int32_t range_classes;   /* distinct (n_range, range spectrum) */
+    int32_t azimuth_classes; /* distinct (L, azimuth spectrum) */
+} sar_batch_info_t;
+
+/* Group the strips into classes (a class shares a kernel schedule -- the
+ * preferred one of its length -- and a filter), build each class's filter
+ * and twiddle tables and segment table, allocate the work buffer
+ * (8 bytes per raw sample) and capture the whole batch into one CUDA graph.
+ * The strip buffers stay owned by the caller and must outlive the batch; the
+ * spectra are copied.  flags must be 0.  Synchronises the device. */
+SAR_API sar_status sar_batch_create(const sar_strip *strips, int32_t count, uint32_t flags, sar_batch *out);
+
+/* Compress every strip of the batch: one graph launch on `stream` (range
+ * passes, one corner turn over all strips, azimuth passes); asynchronous. */
+SAR_API sar_status sar_batch_run(sar_batch batch, sar_stream stream);
+
+/* Sizes of a batch. */
+SAR_API sar_status sar_batch_info(sar_batch batch, sar_batch_info_t *info);
+
+/* Release the batch (no run may still be in flight).  NULL is accepted. */
+SAR_API sar_status sar_batch_destroy(sar_batch batch);
+
+/* ---- serving ----------------------------------------------------------
+ * A continuous-batching request loop (this library's serving layer around
+ * the paper's per-scene compression).  Scenes of a few size classes arrive
+ * over time; a request is admitted as soon as one of max_inflight slots (CUDA
+ * streams) is free and its footprint (raw + image, 16 bytes per sample) fits
+ * the HBM budget left by the requests still running.  An admitted request
+ * allocates its buffers from the server's stream-ordered memory pool, copies
+ * its echo in from the device-resident pool scene of its class (the ingest,
+ * part of its latency), runs sar_rda_process with its class's resident plan,
+ * optionally copies the image out, frees its buffers and records a completion
+ * event.  Requests on different slots overlap on the GPU.  When the oldest
+ * waiting request does not fit, later ones that do fit may pass it for at
+ * most backfill_s seconds. */
+typedef struct {
+    int32_t n_classes;                   /* size classes */
+    int32_t max_inflight;                /* concurrent requests, 1 ... 256 */
+    const int64_t *n_range;              /* [n_classes] powers of two in [256, 16384] */
+    const int64_t *n_az;                 /* [n_classes] powers of two in [256, 16384] */
+    const void *const *pool;             /* [n_classes] device complex64[n_az][n_range] echoes to ingest */
+    const void *const *range_spectrum;   /* [n_classes] device complex64[n_range] */
+    const void *const *az_spectrum;      /* [n_classes] device complex64[n_az] */
+    int64_t hbm_budget_bytes;            /* admission budget */
+    double backfill_s;                   /* how long later requests may pass a blocked head */
+} sar_server_config;
+
+typedef struct {
+    double arrival_s;     /* seconds after the run starts (non-decreasing) */
+    int32_t size_class;   /* index of the request's size class */
+    void *output;         /* device complex64[n_range][n_az] receiving the image, or NULL */
+} sar_request;
+
+typedef struct {
+    double arrival_s;     /* as requested (0 in closed loop) */
+    double admit_s;       /* host time the request was admitted */
+    double done_s;        /* GPU time its work completed; latency = done_s - arrival_s */
+    int32_t status;       /* SAR_OK, or the error of this request */
+} sar_request_result;
+
+#define SAR_SERVE_OPEN_LOOP 0   /* requests arrive at their arrival_s */
+#define SAR_SERVE_CLOSED_LOOP 1 /* every request is waiting at time 0 (saturation) */
+
+typedef struct sar_server_s *sar_server;
+
+/* Create plans for every class (resident until destroy), the slots and the
+ * memory pool.  The pool scenes and spectra must stay valid while the
+ * server exists. */
+SAR_API sar_status sar_server_create(const sar_server_config *config, sar_server *out);
+
+/* Serve n requests and fill results[n]; returns when all are done.  The
+ * calling thread runs the loop (admission, completion polling); the device
+ * must not be used by anything else meanwhile. */
+SAR_API sar_status sar_server_run(sar_server server, const sar_request *requests, int32_t n, int32_t mode,
+                                  sar_request_result *results);
+
+/* Release the server (plans, streams, memory pool).  NULL is accepted. */
+SAR_API sar_status sar_server_destroy(sar_server server);
 
 /* ---- schedules and the autotuner --------------------------------------
  * A schedule fixes how the fused line kernel of one line length N runs: the

@@ -28,6 +28,7 @@ SAR_OK, SAR_ERR_INVALID_ARG, SAR_ERR_UNSUPPORTED, SAR_ERR_OUT_OF_MEMORY, SAR_ERR
 SAR_PREC_FP32 = 0
 SAR_PLAN_UNFOLDED_CORNER_TURN = 1
 SAR_TUNE_FUSED, SAR_TUNE_RANGE_CT = 0, 1
+SAR_SERVE_OPEN_LOOP, SAR_SERVE_CLOSED_LOOP = 0, 1
 
 STATUS_NAMES = {0: "SAR_OK", 1: "SAR_ERR_INVALID_ARG", 2: "SAR_ERR_UNSUPPORTED",
                 3: "SAR_ERR_OUT_OF_MEMORY", 4: "SAR_ERR_CUDA", 5: "SAR_ERR_TIMEOUT"}
@@ -35,10 +36,12 @@ STATUS_NAMES = {0: "SAR_OK", 1: "SAR_ERR_INVALID_ARG", 2: "SAR_ERR_UNSUPPORTED",
 # every entry point declared in include/sar.h
 EXPORTS = ("sar_plan_create", "sar_plan_destroy", "sar_range_compress", "sar_corner_turn",
            "sar_azimuth_compress", "sar_rda_process", "sar_range_compress_oop", "sar_range_compress_ct", "sar_rda_process_oop",
-           "sar_rda_process_host", "sar_make_lfm_spectrum",
+           "sar_rda_process_host", "sar_make_lfm_spectrum", "sar_simulate_echo",
            "sar_fft_lines", "sar_fft_lines_static", "sar_transpose", "sar_schedule_count", "sar_schedule_get",
            "sar_set_preferred_schedule", "sar_set_corner_turn_variant", "sar_plan_create_ex", "sar_plan_get_schedules", "sar_plan_folds_corner_turn", "sar_autotune",
-           "sar_plan_status", "sar_sync", "sar_last_error", "sar_version")
+           "sar_plan_status", "sar_batch_create", "sar_batch_run", "sar_batch_info",
+           "sar_batch_destroy", "sar_server_create", "sar_server_run", "sar_server_destroy",
+           "sar_sync", "sar_last_error", "sar_version")
 
 
 class sar_schedule_desc(ctypes.Structure):
@@ -49,6 +52,34 @@ class sar_schedule_desc(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {f: (getattr(self, f).decode() if f == "name" else getattr(self, f)) for f, _ in self._fields_}
+
+
+class sar_strip(ctypes.Structure):
+    _fields_ = [("n_range", ctypes.c_int64), ("n_az", ctypes.c_int64), ("raw", ctypes.c_void_p),
+                ("image", ctypes.c_void_p), ("range_spectrum", ctypes.c_void_p), ("az_spectrum", ctypes.c_void_p)]
+
+
+class sar_batch_info_t(ctypes.Structure):
+    _fields_ = [("strips", ctypes.c_int64), ("samples", ctypes.c_int64), ("work_bytes", ctypes.c_int64),
+                ("kernels_per_run", ctypes.c_int32), ("range_classes", ctypes.c_int32),
+                ("azimuth_classes", ctypes.c_int32)]
+
+
+class sar_server_config(ctypes.Structure):
+    _fields_ = [("n_classes", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
+                ("n_range", ctypes.POINTER(ctypes.c_int64)), ("n_az", ctypes.POINTER(ctypes.c_int64)),
+                ("pool", ctypes.POINTER(ctypes.c_void_p)), ("range_spectrum", ctypes.POINTER(ctypes.c_void_p)),
+                ("az_spectrum", ctypes.POINTER(ctypes.c_void_p)), ("hbm_budget_bytes", ctypes.c_int64),
+                ("backfill_s", ctypes.c_double)]
+
+
+class sar_request(ctypes.Structure):
+    _fields_ = [("arrival_s", ctypes.c_double), ("size_class", ctypes.c_int32), ("output", ctypes.c_void_p)]
+
+
+class sar_request_result(ctypes.Structure):
+    _fields_ = [("arrival_s", ctypes.c_double), ("admit_s", ctypes.c_double), ("done_s", ctypes.c_double),
+                ("status", ctypes.c_int32)]
 
 
 class sar_filters(ctypes.Structure):
@@ -69,11 +100,21 @@ _SIGS = {
     "sar_rda_process_oop": [_vp, _vp, _vp, _vp, _vp],
     "sar_rda_process_host": [_vp, _vp, _vp, _vp],
     "sar_make_lfm_spectrum": [_i64, _i64, _dbl, _vp, _vp],
+    "sar_simulate_echo": [_i64, _i64, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32, _i64, _dbl, _i64, _dbl, _dbl,
+                          ctypes.c_uint64, _vp, _vp],
     "sar_fft_lines": [_i64, _i64, _vp, _vp, _int, _vp],
     "sar_fft_lines_static": [_i64, _i64, _vp, _vp, _int, _vp],
     "sar_transpose": [_i64, _i64, _vp, _vp, _vp],
     "sar_sync": [_vp],
     "sar_plan_status": [_vp, _vp],
+    "sar_batch_create": [ctypes.POINTER(sar_strip), ctypes.c_int32, ctypes.c_uint32, ctypes.POINTER(_vp)],
+    "sar_batch_run": [_vp, _vp],
+    "sar_batch_info": [_vp, ctypes.POINTER(sar_batch_info_t)],
+    "sar_batch_destroy": [_vp],
+    "sar_server_create": [ctypes.POINTER(sar_server_config), ctypes.POINTER(_vp)],
+    "sar_server_run": [_vp, ctypes.POINTER(sar_request), ctypes.c_int32, ctypes.c_int32,
+                       ctypes.POINTER(sar_request_result)],
+    "sar_server_destroy": [_vp],
     "sar_schedule_get": [ctypes.c_int32, ctypes.POINTER(sar_schedule_desc)],
     "sar_set_preferred_schedule": [ctypes.c_char_p],
     "sar_set_corner_turn_variant": [ctypes.c_int32],
@@ -229,8 +270,8 @@ def sar_plan_destroy(plan: Plan) -> None:
     plan.destroy()
 
 
-def _h(plan):
-    return plan.handle if isinstance(plan, Plan) else plan
+def _h(obj):
+    return obj.handle if hasattr(obj, "handle") else obj
 
 
 def sar_range_compress(plan, data, stream=None) -> None:
@@ -269,6 +310,16 @@ def sar_make_lfm_spectrum(n: int, n_chirp: int, tbp: float, out, stream=None) ->
     _check(_lib.sar_make_lfm_spectrum(n, n_chirp, float(tbp), _ptr(out), _stream(stream)))
 
 
+def sar_simulate_echo(n_az: int, n_range: int, targets, range_chirp, az_chirp, snr_db, seed: int, out,
+                      stream=None) -> None:
+    """targets: [(a0, r0), ...]; range_chirp / az_chirp: (n_c, tbp); snr_db None: no noise."""
+    flat = (ctypes.c_int64 * max(1, 2 * len(targets)))(*[int(v) for t in targets for v in t])
+    _check(_lib.sar_simulate_echo(n_az, n_range, flat, len(targets), int(range_chirp[0]), float(range_chirp[1]),
+                                  int(az_chirp[0]), float(az_chirp[1]),
+                                  float("nan") if snr_db is None else float(snr_db), seed, _ptr(out),
+                                  _stream(stream)))
+
+
 def sar_fft_lines(n: int, n_lines: int, inp, out, inverse: bool = False, stream=None) -> None:
     _check(_lib.sar_fft_lines(n, n_lines, _ptr(inp), _ptr(out), 1 if inverse else 0, _stream(stream)))
 
@@ -288,6 +339,104 @@ def sar_transpose(rows: int, cols: int, inp, out, stream=None) -> None:
 def sar_plan_status(plan, stream=None) -> None:
     """Raise SarError(SAR_ERR_TIMEOUT) if a kernel of the plan gave up a bounded wait."""
     _check(_lib.sar_plan_status(_h(plan), _stream(stream)))
+
+
+class Batch:
+    """An opaque sar_batch handle."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def destroy(self) -> None:
+        if self.handle:
+            _check(_lib.sar_batch_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def sar_batch_create(strips, flags: int = 0) -> Batch:
+    """strips: sequence of dicts with n_range, n_az, raw, image,
+    range_spectrum, az_spectrum (tensors or device addresses)."""
+    arr = (sar_strip * len(strips))()
+    for i, st in enumerate(strips):
+        arr[i] = sar_strip(st["n_range"], st["n_az"], _ptr(st["raw"]), _ptr(st["image"]),
+                           _ptr(st["range_spectrum"]), _ptr(st["az_spectrum"]))
+    h = _vp()
+    _check(_lib.sar_batch_create(arr, len(strips), flags, ctypes.byref(h)))
+    return Batch(h.value)
+
+
+def sar_batch_run(batch, stream=None) -> None:
+    _check(_lib.sar_batch_run(_h(batch), _stream(stream)))
+
+
+def sar_batch_info(batch) -> dict:
+    info = sar_batch_info_t()
+    _check(_lib.sar_batch_info(_h(batch), ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in info._fields_}
+
+
+def sar_batch_destroy(batch) -> None:
+    batch.destroy()
+
+
+class Server:
+    """An opaque sar_server handle; keeps the config arrays alive."""
+
+    def __init__(self, handle: int, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def destroy(self) -> None:
+        if self.handle:
+            _check(_lib.sar_server_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def sar_server_create(classes, hbm_budget_bytes: int, max_inflight: int = 16, backfill_s: float = 0.05) -> Server:
+    """classes: sequence of dicts with n_range, n_az, pool, range_spectrum, az_spectrum."""
+    k = len(classes)
+    nr = (ctypes.c_int64 * k)(*[c["n_range"] for c in classes])
+    na = (ctypes.c_int64 * k)(*[c["n_az"] for c in classes])
+    pool = (ctypes.c_void_p * k)(*[_ptr(c["pool"]) for c in classes])
+    hr = (ctypes.c_void_p * k)(*[_ptr(c["range_spectrum"]) for c in classes])
+    ha = (ctypes.c_void_p * k)(*[_ptr(c["az_spectrum"]) for c in classes])
+    cfg = sar_server_config(k, max_inflight, nr, na, pool, hr, ha, int(hbm_budget_bytes), float(backfill_s))
+    h = _vp()
+    _check(_lib.sar_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return Server(h.value, (nr, na, pool, hr, ha, cfg, classes))
+
+
+def sar_server_run(server, requests, mode: int = SAR_SERVE_OPEN_LOOP) -> list:
+    """requests: sequence of (arrival_s, size_class[, output]); returns a list
+    of dicts (arrival_s, admit_s, done_s, status, latency_s)."""
+    n = len(requests)
+    arr = (sar_request * max(1, n))()
+    for i, r in enumerate(requests):
+        arr[i] = sar_request(float(r[0]), int(r[1]), _ptr(r[2]) if len(r) > 2 and r[2] is not None else None)
+    res = (sar_request_result * max(1, n))()
+    _check(_lib.sar_server_run(_h(server), arr, n, mode, res))
+    out = []
+    for i in range(n):
+        r = res[i]
+        out.append(dict(arrival_s=r.arrival_s, admit_s=r.admit_s, done_s=r.done_s, status=r.status,
+                        latency_s=r.done_s - r.arrival_s))
+    return out
+
+
+def sar_server_destroy(server) -> None:
+    server.destroy()
 
 
 def sar_sync(stream=None) -> None:

@@ -1,0 +1,341 @@
+// Ragged batches: many strips of different sizes compressed by one CUDA-graph
+// launch.
+//
+// A strip is an n_az x n_range raw echo (n_range a power of two, n_az any
+// count); its azimuth lines are transformed at L = max(256, next power of
+// two >= n_az), zero-padded, and the image keeps its n_az columns.  Strips
+// are grouped into classes that share a kernel and a filter: range classes by
+// (n_range, range spectrum), azimuth classes by (L, azimuth spectrum).  One
+// fused launch per class walks a segment table (one segment per strip, the
+// strip's lines concatenated); one batched transpose walks a tile table over
+// all strips.  The whole sequence is captured once into a CUDA graph and
+// replayed by sar_batch_run as a single launch.
+//
+// Data path per strip: range compression raw -> work (batch-owned scratch),
+// corner turn work -> image, azimuth compression in place on image.  The raw
+// echo is only read.
+#include <algorithm>
+#include <new>
+#include <stdio.h>
+#include <string.h>
+#include <vector>
+
+#include "../../include/sar.h"
+#include "registry.h"
+#include "streamed.cuh"
+#include "tables.h"
+
+namespace sar {
+sar_status report_error(sar_status st, const char *msg);
+sar_status validate_device_ptr(const void *p, const char *what);
+sar_status validate_length(int64_t n, const char *what);
+
+struct TSeg {
+    const float2 *in;
+    float2 *out;
+    int64_t rows, cols, tiles_c;
+};
+
+// Corner turn of every strip in one launch: block b is tile b of the
+// concatenated tile lists; 32 x 32 tiles through padded shared memory, as
+// corner_turn_kernel.
+__global__ void __launch_bounds__(256)
+batched_transpose_kernel(const TSeg *segs, const int64_t *tile_begin, int n_seg) {
+    __shared__ float2 tile[32][33];
+    const int k = find_seg(tile_begin, n_seg, (int64_t)blockIdx.x);
+    const TSeg sg = segs[k];
+    const int64_t b = (int64_t)blockIdx.x - tile_begin[k];
+    const int64_t tr = b / sg.tiles_c, tc = b % sg.tiles_c;
+    const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+    const int64_t r0 = tr * 32, c0 = tc * 32;
+#pragma unroll
+    for (int j = 0; j < 32; j += 8) {
+        const int64_t r = r0 + ty + j, c = c0 + tx;
+        if (r < sg.rows && c < sg.cols) tile[ty + j][tx] = sg.in[r * sg.cols + c];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 32; j += 8) {
+        const int64_t c = c0 + ty + j, r = r0 + tx;
+        if (r < sg.rows && c < sg.cols) sg.out[c * sg.rows + r] = tile[tx][ty + j];
+    }
+}
+
+}  // namespace sar
+
+using sar::SchedDesc;
+
+namespace {
+
+int64_t next_pow2(int64_t n) {
+    int64_t p = 1;
+    while (p < n) p <<= 1;
+    return p;
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct LineClass {
+    const SchedDesc *d = nullptr;
+    const void *spectrum = nullptr;
+    int64_t n = 0;
+    bool ragged = false;
+    std::vector<sar::Seg> segs;
+    std::vector<int64_t> begin;   // prefix sums of lines, size segs + 1
+    // device
+    float2 *filt = nullptr, *tw = nullptr;
+    sar::Seg *segs_dev = nullptr;
+    int64_t *begin_dev = nullptr;
+};
+
+// The preferred schedule of length n that has a segment-table kernel.
+const SchedDesc *seg_schedule(int n) {
+    const SchedDesc *p = sar::default_schedule(n);
+    if (p && p->fused_seg) return p;
+    for (int i = 0; i < sar::schedule_count(); ++i)
+        if (sar::schedule_at(i)->n == n && sar::schedule_at(i)->fused_seg) return sar::schedule_at(i);
+    return nullptr;
+}
+
+}  // namespace
+
+struct sar_batch_s {
+    std::vector<LineClass> range, az;
+    std::vector<sar::TSeg> tsegs;
+    std::vector<int64_t> tbegin;
+    sar::TSeg *tsegs_dev = nullptr;
+    int64_t *tbegin_dev = nullptr;
+    void *tables = nullptr;    // filters, twiddles, segment tables
+    void *work = nullptr;      // range-compressed strips
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int device = 0;
+    int64_t samples = 0;       // sum of n_az * n_range
+    int32_t launches = 0;      // kernels in the graph
+    int64_t strips = 0;
+};
+
+static void batch_free(sar_batch b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->tables) cudaFree(b->tables);
+    if (b->work) cudaFree(b->work);
+    delete b;
+}
+
+extern "C" {
+
+sar_status sar_batch_create(const sar_strip *strips, int32_t count, uint32_t flags, sar_batch *out) {
+    if (!out) return sar::report_error(SAR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!strips || count < 1) return sar::report_error(SAR_ERR_INVALID_ARG, "need at least one strip");
+    if (flags != 0) return sar::report_error(SAR_ERR_INVALID_ARG, "flags must be 0");
+    sar_status st;
+    for (int32_t i = 0; i < count; ++i) {
+        const sar_strip &s = strips[i];
+        if ((st = sar::validate_length(s.n_range, "strip n_range")) != SAR_OK) return st;
+        if (s.n_az < 1 || s.n_az > 16384)
+            return sar::report_error(SAR_ERR_UNSUPPORTED, "strip n_az must be in [1, 16384]");
+        if ((st = sar::validate_device_ptr(s.raw, "strip raw")) != SAR_OK) return st;
+        if ((st = sar::validate_device_ptr(s.image, "strip image")) != SAR_OK) return st;
+        if ((st = sar::validate_device_ptr(s.range_spectrum, "strip range_spectrum")) != SAR_OK) return st;
+        if ((st = sar::validate_device_ptr(s.az_spectrum, "strip az_spectrum")) != SAR_OK) return st;
+    }
+    sar_batch b = new (std::nothrow) sar_batch_s;
+    if (!b) return sar::report_error(SAR_ERR_OUT_OF_MEMORY, "host allocation failed");
+    cudaGetDevice(&b->device);
+    b->strips = count;
+
+    // ---- classes and segment tables (host side)
+    size_t work_elems = 0;
+    std::vector<size_t> work_off(count);
+    for (int32_t i = 0; i < count; ++i) {
+        work_off[i] = work_elems;
+        work_elems += (size_t)strips[i].n_az * (size_t)strips[i].n_range;
+    }
+    b->samples = (int64_t)work_elems;
+    auto class_of = [](std::vector<LineClass> &cls, int64_t n, const void *spec) -> LineClass & {
+        for (auto &c : cls)
+            if (c.n == n && c.spectrum == spec) return c;
+        cls.emplace_back();
+        cls.back().n = n;
+        cls.back().spectrum = spec;
+        cls.back().begin.push_back(0);
+        return cls.back();
+    };
+    for (int32_t i = 0; i < count; ++i) {
+        const sar_strip &s = strips[i];
+        const int64_t L = std::max<int64_t>(256, next_pow2(s.n_az));
+        if (L > 16384) {
+            batch_free(b);
+            return sar::report_error(SAR_ERR_UNSUPPORTED, "azimuth transform length above 16384");
+        }
+        LineClass &rc = class_of(b->range, s.n_range, s.range_spectrum);
+        // out: the strip's slice of the work buffer, filled in below
+        rc.segs.push_back(sar::Seg{(const float2 *)s.raw, nullptr, s.n_range, s.n_range, (int32_t)s.n_range, 0});
+        rc.begin.push_back(rc.begin.back() + s.n_az);
+        LineClass &ac = class_of(b->az, L, s.az_spectrum);
+        ac.segs.push_back(sar::Seg{(const float2 *)s.image, (float2 *)s.image, s.n_az, s.n_az, (int32_t)s.n_az, 0});
+        ac.begin.push_back(ac.begin.back() + s.n_range);
+        if (s.n_az < L) ac.ragged = true;
+        b->tsegs.push_back(sar::TSeg{nullptr, (float2 *)s.image, s.n_az, s.n_range, (s.n_range + 31) / 32});
+    }
+    b->tbegin.push_back(0);
+    for (auto &t : b->tsegs) b->tbegin.push_back(b->tbegin.back() + ((t.rows + 31) / 32) * t.tiles_c);
+    for (auto *cls : {&b->range, &b->az})
+        for (auto &c : *cls) {
+            c.d = seg_schedule((int)c.n);
+            if (!c.d) {
+                batch_free(b);
+                return sar::report_error(SAR_ERR_UNSUPPORTED, "no segment-table kernel for a strip length");
+            }
+        }
+
+    // ---- device memory: one block of tables, one work buffer
+    size_t tab = 0;
+    auto reserve = [&](size_t bytes) {
+        const size_t o = tab;
+        tab += align_up(bytes);
+        return o;
+    };
+    std::vector<size_t> off_f, off_t, off_s, off_b;
+    int64_t max_n = 0;
+    for (auto *cls : {&b->range, &b->az})
+        for (auto &c : *cls) {
+            off_f.push_back(reserve(sizeof(float2) * c.n));
+            off_t.push_back(reserve(sizeof(float2) * c.d->tw_elems));
+            off_s.push_back(reserve(sizeof(sar::Seg) * c.segs.size()));
+            off_b.push_back(reserve(sizeof(int64_t) * c.begin.size()));
+            max_n = std::max(max_n, c.n);
+        }
+    const size_t off_ts = reserve(sizeof(sar::TSeg) * b->tsegs.size());
+    const size_t off_tb = reserve(sizeof(int64_t) * b->tbegin.size());
+    const size_t off_ix = reserve(sizeof(int32_t) * max_n);
+    if (cudaMalloc(&b->tables, tab) != cudaSuccess || cudaMalloc(&b->work, sizeof(float2) * work_elems) != cudaSuccess) {
+        cudaGetLastError();
+        batch_free(b);
+        return sar::report_error(SAR_ERR_OUT_OF_MEMORY, "batch tables or work buffer");
+    }
+    char *base = (char *)b->tables;
+    size_t ci = 0;
+    float2 *work = (float2 *)b->work;
+    {
+        // range segments write to each strip's slice of the work buffer, which
+        // the transpose then reads
+        size_t strip = 0;
+        std::vector<size_t> seen(b->range.size(), 0);
+        for (int32_t i = 0; i < count; ++i) {
+            const sar_strip &s = strips[i];
+            for (size_t r = 0; r < b->range.size(); ++r) {
+                LineClass &c = b->range[r];
+                if (c.n == s.n_range && c.spectrum == s.range_spectrum) {
+                    c.segs[seen[r]++].out = work + work_off[i];
+                    break;
+                }
+            }
+            b->tsegs[strip++].in = work + work_off[i];
+        }
+    }
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();   // the caller's spectra are ready
+    int32_t *idx_dev = (int32_t *)(base + off_ix);
+    std::vector<int32_t> idx;
+    for (auto *cls : {&b->range, &b->az})
+        for (auto &c : *cls) {
+            if (e != cudaSuccess) break;
+            c.filt = (float2 *)(base + off_f[ci]);
+            c.tw = (float2 *)(base + off_t[ci]);
+            c.segs_dev = (sar::Seg *)(base + off_s[ci]);
+            c.begin_dev = (int64_t *)(base + off_b[ci]);
+            ++ci;
+            if ((e = c.d->prepare()) != cudaSuccess) break;
+            if ((e = sar::build_twiddles(*c.d, c.tw, s)) != cudaSuccess) break;
+            idx.assign(c.n, 0);
+            sar::filter_slot_to_k(*c.d, idx.data());
+            if ((e = cudaMemcpyAsync(idx_dev, idx.data(), sizeof(int32_t) * c.n, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+                break;
+            if ((e = sar::build_filter(*c.d, (const float2 *)c.spectrum, c.filt, idx_dev, s)) != cudaSuccess) break;
+            if ((e = cudaMemcpyAsync(c.segs_dev, c.segs.data(), sizeof(sar::Seg) * c.segs.size(), cudaMemcpyHostToDevice,
+                                     s)) != cudaSuccess)
+                break;
+            if ((e = cudaMemcpyAsync(c.begin_dev, c.begin.data(), sizeof(int64_t) * c.begin.size(),
+                                     cudaMemcpyHostToDevice, s)) != cudaSuccess)
+                break;
+            e = cudaStreamSynchronize(s);   // idx is reused by the next class
+        }
+    b->tsegs_dev = (sar::TSeg *)(base + off_ts);
+    b->tbegin_dev = (int64_t *)(base + off_tb);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->tsegs_dev, b->tsegs.data(), sizeof(sar::TSeg) * b->tsegs.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->tbegin_dev, b->tbegin.data(), sizeof(int64_t) * b->tbegin.size(), cudaMemcpyHostToDevice,
+                            s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+
+    // ---- capture the whole batch into one graph
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t le = cudaSuccess;
+        for (auto &c : b->range) {
+            if (le == cudaSuccess)
+                le = c.d->fused_seg(c.segs_dev, c.begin_dev, (int)c.segs.size(), c.begin.back(), false, c.filt, c.tw, s);
+            ++b->launches;
+        }
+        if (le == cudaSuccess) {
+            sar::batched_transpose_kernel<<<(unsigned)b->tbegin.back(), 256, 0, s>>>(b->tsegs_dev, b->tbegin_dev,
+                                                                                    (int)b->tsegs.size());
+            le = cudaGetLastError();
+            ++b->launches;
+        }
+        for (auto &c : b->az) {
+            if (le == cudaSuccess)
+                le = c.d->fused_seg(c.segs_dev, c.begin_dev, (int)c.segs.size(), c.begin.back(), c.ragged, c.filt, c.tw,
+                                    s);
+            ++b->launches;
+        }
+        e = cudaStreamEndCapture(s, &b->graph);
+        if (e == cudaSuccess && le != cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (s) cudaStreamDestroy(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        batch_free(b);
+        char msg[256];
+        snprintf(msg, sizeof(msg), "batch set-up failed: %s", cudaGetErrorString(e));
+        return sar::report_error(SAR_ERR_CUDA, msg);
+    }
+    *out = b;
+    return SAR_OK;
+}
+
+sar_status sar_batch_run(sar_batch b, sar_stream stream) {
+    if (!b) return sar::report_error(SAR_ERR_INVALID_ARG, "batch is NULL");
+    cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        char msg[256];
+        snprintf(msg, sizeof(msg), "graph launch: %s", cudaGetErrorString(e));
+        return sar::report_error(SAR_ERR_CUDA, msg);
+    }
+    return SAR_OK;
+}
+
+sar_status sar_batch_info(sar_batch b, sar_batch_info_t *info) {
+    if (!b || !info) return sar::report_error(SAR_ERR_INVALID_ARG, "batch or info is NULL");
+    info->strips = b->strips;
+    info->samples = b->samples;
+    info->kernels_per_run = b->launches;
+    info->range_classes = (int32_t)b->range.size();
+    info->azimuth_classes = (int32_t)b->az.size();
+    info->work_bytes = b->samples * 8;
+    return SAR_OK;
+}
+
+sar_status sar_batch_destroy(sar_batch b) {
+    batch_free(b);
+    return SAR_OK;
+}
+
+}  // extern "C"

@@ -131,7 +131,8 @@ constexpr SchedDesc make_persistent_desc(const char *name) {
                      &launch_dft<SC, 1>,
                      &prepare_persistent<SC>,
                      nullptr,
-                     0};
+                     0,
+                     nullptr};
 }
 
 // --- group-streamed schedules ---------------------------------------------
@@ -151,6 +152,14 @@ cudaError_t prepare_streamed() {
         else
             e = cudaFuncSetAttribute(fused_streamed_kernel<SC, LPB, ROLL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      smem);
+        if (e != cudaSuccess) return e;
+    }
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(fused_seg_kernel<SC, LPB, ROLL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(fused_seg_kernel<SC, LPB, ROLL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem);
         if (e != cudaSuccess) return e;
     }
     if constexpr (QL > 0) {
@@ -221,6 +230,20 @@ cudaError_t launch_range_ct_cluster(const float2 *in, float2 *img, int64_t n_lin
     return cudaLaunchKernelEx(&cfg, fused_range_ct_cluster_kernel<SC, QC, ROLL>, in, img, ld_in, ld_img, filt, tw);
 }
 
+template <class SC, int LPB, bool ROLL>
+cudaError_t launch_seg(const Seg *segs, const int64_t *line_begin, int n_seg, int64_t n_lines, bool ragged,
+                       const float2 *filt, const float2 *tw, cudaStream_t st) {
+    if (n_lines <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((n_lines + LPB - 1) / LPB);
+    if (ragged)
+        fused_seg_kernel<SC, LPB, ROLL, true><<<blocks, SC::T * LPB, smem_bytes_of<SC, LPB>(), st>>>(
+            segs, line_begin, n_seg, n_lines, filt, tw);
+    else
+        fused_seg_kernel<SC, LPB, ROLL, false><<<blocks, SC::T * LPB, smem_bytes_of<SC, LPB>(), st>>>(
+            segs, line_begin, n_seg, n_lines, filt, tw);
+    return cudaGetLastError();
+}
+
 // QL > 0: fold with QL lines per block; QL < 0: fold with clusters of -QL blocks
 template <class SC, int LPB, bool ROLL, int QL = 0>
 constexpr SchedDesc make_streamed_desc(const char *name) {
@@ -241,7 +264,8 @@ constexpr SchedDesc make_streamed_desc(const char *name) {
                      &prepare_streamed<SC, LPB, ROLL, QL>,
                      QL > 0 ? &launch_range_ct<SC, ROLL, (QL > 0 ? QL : 2)>
                             : (QL < 0 ? &launch_range_ct_cluster<SC, (QL < 0 ? -QL : 4), ROLL> : nullptr),
-                     QL > 0 ? QL : -QL};
+                     QL > 0 ? QL : -QL,
+                     &launch_seg<SC, LPB, ROLL>};
 }
 
 template <class SC, int LPB>
@@ -262,7 +286,8 @@ constexpr SchedDesc make_desc(const char *name) {
                      &launch_dft<SC, LPB>,
                      &prepare_sched<SC, LPB>,
                      nullptr,
-                     0};
+                     0,
+                     nullptr};
 }
 
 }  // namespace sar

@@ -25,6 +25,12 @@ typedef cudaError_t (*prep_fn)(void);
 typedef cudaError_t (*fused_ct_fn)(const float2 *in, float2 *img, int64_t n_lines, int64_t ld_in, int64_t ld_img,
                                    const float2 *filt, const float2 *tw, cudaStream_t st);
 
+// Fused pass over a segment table (ragged batches); segs/line_begin are
+// device arrays (n_seg segments, n_seg + 1 prefix sums of their lines).
+struct Seg;
+typedef cudaError_t (*seg_fn)(const Seg *segs, const int64_t *line_begin, int n_seg, int64_t n_lines, bool ragged,
+                              const float2 *filt, const float2 *tw, cudaStream_t st);
+
 struct SchedDesc {
     const char *name;
     int n, e, r1, r2, r3;   // r3 == 1 for two-pass schedules
@@ -39,6 +45,7 @@ struct SchedDesc {
     prep_fn prepare;        // raises the dynamic shared-memory limit where needed
     fused_ct_fn fused_ct;   // nullptr: no folded corner turn for this schedule
     int ct_lines;           // lines per block of fused_ct (n_lines must be a multiple)
+    seg_fn fused_seg;       // nullptr: no segment-table kernel for this schedule
 };
 
 // All compiled schedules (one table per translation unit).

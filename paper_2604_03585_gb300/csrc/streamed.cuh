@@ -63,9 +63,19 @@ __device__ __forceinline__ void streamed_mid_pass(float2* sm, const float2* tw, 
 // pass 1 from HBM, the middle passes, the last forward pass with the filter
 // multiply and the first inverse pass, and the inverse middle passes.  On
 // return the line sits in shared memory ready for the inverse pass 1.
-template <class SC, int LPB, bool ROLL>
+// Element i of a line that holds `valid` stored samples (zero beyond them:
+// a zero-padded transform of a ragged line).
+template <bool RAGGED>
+__device__ __forceinline__ float2 line_at(const float2* src, int i, int valid) {
+    if constexpr (RAGGED)
+        return i < valid ? src[i] : make_float2(0.f, 0.f);
+    else
+        return src[i];
+}
+
+template <class SC, int LPB, bool ROLL, bool RAGGED = false>
 __device__ __forceinline__ void streamed_until_last(const float2* src, float2* sm, const float2* filt,
-                                                    const float2* tw, int t, int lib) {
+                                                    const float2* tw, int t, int lib, int valid = SC::N) {
     constexpr int R1 = SC::R1, S1 = SC::S1, G1 = SC::E / R1;
     constexpr int RL = SC::RL, GL = SC::E / RL;
 
@@ -73,14 +83,14 @@ __device__ __forceinline__ void streamed_until_last(const float2* src, float2* s
     //      next group's loads in flight during the current group's arithmetic
     float2 cur[R1];
 #pragma unroll
-    for (int r = 0; r < R1; ++r) cur[r] = src[t + r * S1];
+    for (int r = 0; r < R1; ++r) cur[r] = line_at<RAGGED>(src, t + r * S1, valid);
 #pragma unroll(ROLL ? 1 : G1)
     for (int s = 0; s < G1; ++s) {
         const int lo = t + SC::T * s;
         float2 nxt[R1];
         if (s + 1 < G1) {
 #pragma unroll
-            for (int r = 0; r < R1; ++r) nxt[r] = src[lo + SC::T + r * S1];
+            for (int r = 0; r < R1; ++r) nxt[r] = line_at<RAGGED>(src, lo + SC::T + r * S1, valid);
         }
         dft_reg<R1, false>(cur);
         grp_twiddle<R1, S1, false>(tw, lo, cur);
@@ -137,6 +147,58 @@ __device__ __forceinline__ void fused_streamed_body(const float2* in, float2* ou
         dft_reg<R1, true>(x);
 #pragma unroll
         for (int r = 0; r < R1; ++r) dst[lo + r * S1] = x[r];
+    }
+}
+
+// Fused line compression over a table of segments (a ragged batch): segment
+// k covers lines [line_begin[k], line_begin[k+1]) of the launch; its line j
+// is read from in + j*ld_in (valid samples, zero-padded to N) and written to
+// out + j*ld_out (the first `valid` samples).  Every line finds its segment
+// by binary search over the prefix sums.
+struct Seg {
+    const float2* in;
+    float2* out;
+    int64_t ld_in, ld_out;
+    int32_t valid, pad;
+};
+
+__device__ __forceinline__ int find_seg(const int64_t* line_begin, int n_seg, int64_t g) {
+    int lo = 0, hi = n_seg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (line_begin[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <class SC, int LPB, bool ROLL, bool RAGGED>
+__global__ void __launch_bounds__(SC::T * LPB)
+fused_seg_kernel(const Seg* segs, const int64_t* line_begin, int n_seg, int64_t n_lines, const float2* filt,
+                 const float2* tw) {
+    extern __shared__ float2 smem_dyn[];
+    const int lib = threadIdx.x / SC::T;
+    const int t = threadIdx.x % SC::T;
+    const int64_t g = (int64_t)blockIdx.x * LPB + lib;
+    if (g >= n_lines) return;
+    const int k = find_seg(line_begin, n_seg, g);
+    const Seg sg = segs[k];
+    const int64_t j = g - line_begin[k];
+    float2* sm = smem_dyn + lib * SC::SMEM_ELEMS;
+    float2* dst = sg.out + j * sg.ld_out;
+    constexpr int R1 = SC::R1, S1 = SC::S1, G1 = SC::E / R1;
+    streamed_until_last<SC, LPB, ROLL, RAGGED>(sg.in + j * sg.ld_in, sm, filt, tw, t, lib, sg.valid);
+#pragma unroll(ROLL ? 1 : G1)
+    for (int s = 0; s < G1; ++s) {
+        const int lo = t + SC::T * s;
+        float2 x[R1];
+        grp_smem_load<R1, S1>(sm, lo, SC::PADSH, x);
+        grp_twiddle<R1, S1, true>(tw, lo, x);
+        dft_reg<R1, true>(x);
+#pragma unroll
+        for (int r = 0; r < R1; ++r) {
+            const int i = lo + r * S1;
+            if (!RAGGED || i < sg.valid) dst[i] = x[r];
+        }
     }
 }
 

@@ -192,11 +192,75 @@ def next_pow2(n: int) -> int:
 
 
 def strip_spec(seed: int, n_range: int, n_az: int, n_targets: int, snr_db: float = 10.0) -> SceneSpec:
-    """A strip of a ragged batch: azimuth transform length L = next power of two
-    >= n_az, chirps scaled to the strip, seeded targets kept at least half a
-    chirp from every edge so that no echo wraps around the strip."""
-    l_az = next_pow2(n_az)
-    rc, ac = scaled_chirps(n_range, l_az)
-    tg = place_targets(seed, n_az, n_range, n_targets, margin_az=ac[0] // 2 + 1,
-                       margin_r=rc[0] // 2 + 1, min_sep=min(256, max(8, n_az // 4)))
-    return SceneSpec(n_az, n_range, tg, rc, ac, snr_db, seed, l_az=l_az)
+    """A strip of a ragged batch: azimuth transform length L = max(256, next
+    power of two >= n_az), chirps scaled to the strip (the azimuth chirp no
+    longer than the strip), seeded targets kept at least half a chirp from
+    every edge where the strip is tall enough, so that no echo wraps."""
+    l_az = max(256, next_pow2(n_az))
+    (ncr, tbr), (nca, tba) = scaled_chirps(n_range, l_az)
+    if nca > n_az:
+        nca = n_az
+        tba = nca / 8.0
+    m_az = nca // 2 + 1
+    m_r = ncr // 2 + 1
+    if 2 * m_az >= n_az:
+        m_az = 0
+    tg = place_targets(seed, n_az, n_range, n_targets, margin_az=m_az, margin_r=m_r,
+                       min_sep=min(256, max(1, n_az // 4)))
+    return SceneSpec(n_az, n_range, tg, (ncr, tbr), (nca, tba), snr_db, seed, l_az=l_az)
+
+
+STREAM_BATCH = 3
+STREAM_REQUESTS = 5
+
+
+def ragged_batch_specs(seed: int = 4, count: int = 64) -> list:
+    """The ragged batch: `count` strips, range length drawn from {1024, 2048,
+    4096, 8192, 16384}, azimuth line count uniform in [256, 4096], 1 to 8
+    targets, chirps scaled to each strip; strip i uses uniforms 3i .. 3i+2 of
+    the batch stream and its own seed for targets and noise."""
+    u = uniform(seed, STREAM_BATCH, 0, 3 * count)
+    out = []
+    for i in range(count):
+        n_range = 1024 << int(u[3 * i] * 5)
+        n_az = 256 + int(u[3 * i + 1] * (4096 - 256 + 1))
+        n_t = 1 + int(u[3 * i + 2] * 8)
+        out.append(strip_spec(seed * 1000 + i, n_range, n_az, n_t))
+    return out
+
+
+SERVING_SIZES = (2048, 4096, 8192, 16384)
+SERVING_MIX = (0.70, 0.25, 0.04, 0.01)
+
+
+def serving_requests(seed: int = 5, n: int = 2000, variants: int = 2) -> list:
+    """Size class and scene variant of each of n requests: size drawn with
+    probabilities SERVING_MIX over SERVING_SIZES (uniform 2i of the request
+    stream), variant uniform over `variants` (uniform 2i+1).  Returns
+    [(size_index, variant), ...]."""
+    u = uniform(seed, STREAM_REQUESTS, 0, 2 * n)
+    edges = np.cumsum(SERVING_MIX)
+    out = []
+    for i in range(n):
+        k = int(np.searchsorted(edges, u[2 * i], side="right"))
+        out.append((min(k, len(SERVING_SIZES) - 1), int(u[2 * i + 1] * variants)))
+    return out
+
+
+def poisson_arrivals(seed: int, n: int, rate: float) -> np.ndarray:
+    """n arrival times (seconds) of a Poisson process of `rate` per second:
+    exponential gaps -ln(1 - u)/rate from stream 6."""
+    u = uniform(seed, 6, 0, n)
+    return np.cumsum(-np.log1p(-u) / rate)
+
+
+def serving_scene(size: int, variant: int, seed: int = 5) -> SceneSpec:
+    """Pool scene of a serving size class: 1 to 16 seeded targets, chirps
+    scaled as for the strips (range n/8 with TBP n/16, azimuth n/4 with TBP
+    n/32), 10 dB SNR."""
+    s = seed * 100 + variant * 10 + SERVING_SIZES.index(size) if size in SERVING_SIZES else seed * 100 + variant
+    n_t = 1 + int(uniform(s, STREAM_TARGETS, 10 ** 6, 1)[0] * 16)
+    rc, ac = scaled_chirps(size, size)
+    tg = place_targets(s, size, size, n_t, margin_az=ac[0] // 2 + 1, margin_r=rc[0] // 2 + 1,
+                       min_sep=min(256, size // 32))
+    return SceneSpec(size, size, tg, rc, ac, 10.0, s)

@@ -1,0 +1,106 @@
+"""GPU: the device echo simulator against the host generator, and ragged
+batches (strips of mixed sizes in one CUDA-graph launch) against the oracle."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import sarsim
+from oracle import metrics as M
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+NTHREADS = max(1, os.cpu_count() or 1)
+
+
+@pytest.fixture(scope="module")
+def sar(built_lib):
+    import paper_2604_03585_gb300 as sar
+    assert torch.cuda.is_available(), "gpu tests need a CUDA device"
+    torch.cuda.set_device(0)
+    return sar
+
+
+@pytest.mark.parametrize("spec", [sarsim.scene_256(),
+                                  sarsim.SceneSpec(300, 512, [(10, 500), (150, 256), (299, 3)], (128, 64.0),
+                                                   (64, 8.0), 10.0, 11),
+                                  sarsim.SceneSpec(64, 1024, [(32, 512)], (1024, 512.0), (64, 16.0), None, 3)],
+                         ids=["scene256", "wrapping", "noise_free"])
+def test_device_simulator_matches_host_generator(sar, spec):
+    host = sarsim.echo(spec)
+    out = torch.empty((spec.n_az, spec.n_range), dtype=torch.complex64, device="cuda")
+    sar.sar_simulate_echo(spec.n_az, spec.n_range, spec.targets, spec.range_chirp, spec.az_chirp, spec.snr_db,
+                          spec.seed, out)
+    dev = out.cpu().numpy()
+    same = np.mean(dev == host)
+    assert same > 0.999, same
+    diff = np.abs(dev.astype(np.complex128) - host.astype(np.complex128))
+    scale = np.maximum(np.abs(host.astype(np.complex128)), 1e-30)
+    assert np.max(diff / scale) < 2.5e-7
+
+
+def make_strips(sar, orc, shapes, seed=4):
+    strips, keep, specs = [], [], []
+    hr, ha = {}, {}
+    for i, (n_range, n_az) in enumerate(shapes):
+        spec = sarsim.strip_spec(seed * 100 + i, n_range, n_az, 1 + i % 4)
+        raw = sarsim.echo(spec)
+        L = spec.l_az if spec.l_az >= 256 else 256
+        spec.l_az = L
+        if n_range not in hr:
+            hr[n_range] = torch.from_numpy(
+                orc.matched_filter(n_range, sarsim.lfm_chirp(*spec.range_chirp)).astype(np.complex64)).cuda()
+        if L not in ha:
+            ha[L] = torch.from_numpy(orc.matched_filter(L, sarsim.lfm_chirp(*spec.az_chirp)).astype(np.complex64)).cuda()
+        raw_d = torch.from_numpy(raw).cuda()
+        img_d = torch.empty((n_range, n_az), dtype=torch.complex64, device="cuda")
+        strips.append(dict(n_range=n_range, n_az=n_az, raw=raw_d, image=img_d, range_spectrum=hr[n_range],
+                           az_spectrum=ha[L]))
+        keep.append((raw, raw_d, img_d))
+        specs.append(spec)
+    return strips, keep, specs, hr, ha
+
+
+def test_ragged_batch_vs_oracle(sar):
+    orc = oracle.default()
+    shapes = [(1024, 300), (256, 256), (4096, 777), (1024, 1000), (2048, 129), (256, 1), (512, 4096), (1024, 300)]
+    strips, keep, specs, hr, ha = make_strips(sar, orc, shapes)
+    batch = sar.sar_batch_create(strips)
+    info = sar.sar_batch_info(batch)
+    assert info["strips"] == len(shapes)
+    assert info["samples"] == sum(a * b for a, b in shapes)
+    assert info["range_classes"] == 5 and info["azimuth_classes"] == 4
+    sar.sar_batch_run(batch)
+    sar.sar_sync()
+    for (raw, raw_d, img_d), spec, st in zip(keep, specs, strips):
+        img = img_d.cpu().numpy()
+        assert np.array_equal(raw_d.cpu().numpy(), raw)            # raw is read only
+        Hr = hr[spec.n_range].cpu().numpy().astype(np.complex128)
+        Ha = ha[spec.l_az].cpu().numpy().astype(np.complex128)
+        ref = orc.rda(raw, Hr, Ha, l_az=spec.l_az, nthreads=NTHREADS)
+        assert M.rel_l2(img, ref) < 2e-5, (spec.n_range, spec.n_az)
+        for (a0, r0) in spec.targets:
+            if spec.n_az >= 64:
+                assert M.peak(img, (r0, a0)) == M.peak(ref, (r0, a0))
+    # a second run of the same graph gives the same images
+    first = [k[2].clone() for k in keep]
+    sar.sar_batch_run(batch)
+    sar.sar_sync()
+    for a, k in zip(first, keep):
+        assert torch.equal(a, k[2])
+    batch.destroy()
+
+
+def test_batch_refuses_bad_strips(sar):
+    x = torch.empty(1024, dtype=torch.complex64, device="cuda")
+    bad = [dict(n_range=1000, n_az=4, raw=x, image=x, range_spectrum=x, az_spectrum=x)]
+    with pytest.raises(sar.SarError) as e:
+        sar.sar_batch_create(bad)
+    assert e.value.status == sar.SAR_ERR_UNSUPPORTED
+    bad = [dict(n_range=256, n_az=20000, raw=x, image=x, range_spectrum=x, az_spectrum=x)]
+    with pytest.raises(sar.SarError):
+        sar.sar_batch_create(bad)
+    with pytest.raises(sar.SarError):
+        sar.sar_batch_create([dict(n_range=256, n_az=4, raw=np.zeros(4, np.complex64), image=x,
+                                   range_spectrum=x, az_spectrum=x)])
