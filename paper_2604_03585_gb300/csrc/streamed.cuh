@@ -65,12 +65,14 @@ __device__ __forceinline__ void streamed_mid_pass(float2* sm, const float2* tw, 
 // return the line sits in shared memory ready for the inverse pass 1.
 // Element i of a line that holds `valid` stored samples (zero beyond them:
 // a zero-padded transform of a ragged line).
+// Line samples are read once: streaming loads (evict-first), so that they
+// do not push the twiddle and filter tables out of L1.
 template <bool RAGGED>
 __device__ __forceinline__ float2 line_at(const float2* src, int i, int valid) {
     if constexpr (RAGGED)
-        return i < valid ? src[i] : make_float2(0.f, 0.f);
+        return i < valid ? __ldcs(src + i) : make_float2(0.f, 0.f);
     else
-        return src[i];
+        return __ldcs(src + i);
 }
 
 template <class SC, int LPB, bool ROLL, bool RAGGED = false>
@@ -146,7 +148,7 @@ __device__ __forceinline__ void fused_streamed_body(const float2* in, float2* ou
         grp_twiddle<R1, S1, true>(tw, lo, x);
         dft_reg<R1, true>(x);
 #pragma unroll
-        for (int r = 0; r < R1; ++r) dst[lo + r * S1] = x[r];
+        for (int r = 0; r < R1; ++r) __stcs(dst + lo + r * S1, x[r]);
     }
 }
 
@@ -197,7 +199,7 @@ fused_seg_kernel(const Seg* segs, const int64_t* line_begin, int n_seg, int64_t 
 #pragma unroll
         for (int r = 0; r < R1; ++r) {
             const int i = lo + r * S1;
-            if (!RAGGED || i < sg.valid) dst[i] = x[r];
+            if (!RAGGED || i < sg.valid) __stcs(dst + i, x[r]);
         }
     }
 }
@@ -304,7 +306,7 @@ __device__ __forceinline__ void fused_range_ct_cluster_body(const float2* in, fl
         const int p = idx % LPN;
         const float2 c0 = cluster.map_shared_rank(sm, 2 * p)[n];
         const float2 c1 = cluster.map_shared_rank(sm, 2 * p + 1)[n];
-        *reinterpret_cast<float4*>(img + (int64_t)n * ld_img + a0 + 2 * p) = make_float4(c0.x, c0.y, c1.x, c1.y);
+        __stcs(reinterpret_cast<float4*>(img + (int64_t)n * ld_img + a0 + 2 * p), make_float4(c0.x, c0.y, c1.x, c1.y));
     }
     cluster.sync();
 }
