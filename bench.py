@@ -227,6 +227,29 @@ def reference_arm(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
+# the unfused comparison pipeline (paper Table II's baseline, on the GPU)
+# ---------------------------------------------------------------------------
+
+def unfused_bench(sar, plan, raw, work, image, stream, fused_ms: float, reps: int = 50) -> dict:
+    import torch
+    times = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for i in range(reps + 3):
+        work.copy_(raw)                     # the unfused path compresses raw in place: restore it (untimed)
+        e0.record(stream)
+        sar.sar_rda_process_unfused(plan, work, image, stream)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= 3:
+            times.append(e0.elapsed_time(e1))
+    times.sort()
+    ms = times[len(times) // 2]
+    return {"ms_per_scene": ms, "kernels_per_scene": 7, "fusion_speedup": ms / fused_ms,
+            "note": "per pass: FFT kernel, spectrum-multiply kernel, IFFT kernel (6 transfers per line), plus "
+                    "the corner turn; median of 50 scenes, raw restored outside the timed events"}
+
+
+# ---------------------------------------------------------------------------
 # ragged batch: 64 strips of mixed sizes in one CUDA-graph launch
 # ---------------------------------------------------------------------------
 
@@ -474,6 +497,7 @@ def main():
 
     extras = {}
     if not args.no_extras:
+        extras["unfused"] = unfused_bench(sar, plan, raws[0], work, image, stream, ms_step)
         extras["ragged_batch"] = ragged_batch_bench(sar, roofline, dev, stream, peak)
         extras["serving"] = serving_bench(sar, dev, stream)
 

@@ -142,6 +142,16 @@ SAR_API sar_status sar_range_compress_ct(sar_plan plan, const void *raw, void *i
  * complex64[n_range][n_az].  The three buffers must not overlap. */
 SAR_API sar_status sar_rda_process_oop(sar_plan plan, const void *raw, void *work, void *image, sar_stream stream);
 
+/* The unfused comparison pipeline the paper's fused kernel replaces (Sec.
+ * II-B, Fig. 1 top; Table II's "unfused baseline", here entirely on the
+ * GPU): per pass a forward FFT kernel, a spectrum multiply kernel and an
+ * inverse FFT kernel, six device-memory transfers per line instead of two.
+ * Same arguments, layouts and results (to rounding) as the fused calls;
+ * raw is compressed in place. */
+SAR_API sar_status sar_range_compress_unfused(sar_plan plan, void *data, sar_stream stream);
+SAR_API sar_status sar_azimuth_compress_unfused(sar_plan plan, void *data, sar_stream stream);
+SAR_API sar_status sar_rda_process_unfused(sar_plan plan, void *raw, void *image, sar_stream stream);
+
 /* The same three steps on HOST buffers: copies raw to the device, runs
  * sar_rda_process, copies the image back, and returns once the image is in
  * host memory.  raw: host complex64[n_az][n_range] (not modified);

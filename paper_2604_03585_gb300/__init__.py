@@ -36,6 +36,7 @@ STATUS_NAMES = {0: "SAR_OK", 1: "SAR_ERR_INVALID_ARG", 2: "SAR_ERR_UNSUPPORTED",
 # every entry point declared in include/sar.h
 EXPORTS = ("sar_plan_create", "sar_plan_destroy", "sar_range_compress", "sar_corner_turn",
            "sar_azimuth_compress", "sar_rda_process", "sar_range_compress_oop", "sar_range_compress_ct", "sar_rda_process_oop",
+           "sar_range_compress_unfused", "sar_azimuth_compress_unfused", "sar_rda_process_unfused",
            "sar_rda_process_host", "sar_make_lfm_spectrum", "sar_simulate_echo",
            "sar_fft_lines", "sar_fft_lines_static", "sar_transpose", "sar_schedule_count", "sar_schedule_get",
            "sar_set_preferred_schedule", "sar_set_corner_turn_variant", "sar_plan_create_ex", "sar_plan_get_schedules", "sar_plan_folds_corner_turn", "sar_autotune",
@@ -97,6 +98,9 @@ _SIGS = {
     "sar_rda_process": [_vp, _vp, _vp, _vp],
     "sar_range_compress_oop": [_vp, _vp, _vp, _vp],
     "sar_range_compress_ct": [_vp, _vp, _vp, _vp],
+    "sar_range_compress_unfused": [_vp, _vp, _vp],
+    "sar_azimuth_compress_unfused": [_vp, _vp, _vp],
+    "sar_rda_process_unfused": [_vp, _vp, _vp, _vp],
     "sar_rda_process_oop": [_vp, _vp, _vp, _vp, _vp],
     "sar_rda_process_host": [_vp, _vp, _vp, _vp],
     "sar_make_lfm_spectrum": [_i64, _i64, _dbl, _vp, _vp],
@@ -296,6 +300,18 @@ def sar_range_compress_oop(plan, inp, out, stream=None) -> None:
 
 def sar_range_compress_ct(plan, raw, image, stream=None) -> None:
     _check(_lib.sar_range_compress_ct(_h(plan), _ptr(raw), _ptr(image), _stream(stream)))
+
+
+def sar_range_compress_unfused(plan, data, stream=None) -> None:
+    _check(_lib.sar_range_compress_unfused(_h(plan), _ptr(data), _stream(stream)))
+
+
+def sar_azimuth_compress_unfused(plan, data, stream=None) -> None:
+    _check(_lib.sar_azimuth_compress_unfused(_h(plan), _ptr(data), _stream(stream)))
+
+
+def sar_rda_process_unfused(plan, raw, image, stream=None) -> None:
+    _check(_lib.sar_rda_process_unfused(_h(plan), _ptr(raw), _ptr(image), _stream(stream)))
 
 
 def sar_rda_process_oop(plan, raw, work, image, stream=None) -> None:

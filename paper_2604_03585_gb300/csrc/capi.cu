@@ -78,6 +78,7 @@ struct LinePlan {
     const SchedDesc *sched = nullptr;
     float2 *filt = nullptr;  // n complex, register order, 1/N folded in
     float2 *tw = nullptr;    // twiddle tables
+    float2 *filt_nat = nullptr;  // n complex, natural order, 1/N folded in (unfused path)
 };
 
 // Per-device cache of twiddle tables for the stand-alone FFT entry points.
@@ -216,7 +217,9 @@ sar_status sar_plan_create_ex(int64_t n_range, int64_t n_az, const sar_filters *
     const size_t o_ta = o_fa + align_up(sizeof(float2) * (size_t)n_az);
     const size_t o_ix = o_ta + align_up(sizeof(float2) * (size_t)da->tw_elems);
     const size_t o_st = o_ix + align_up(sizeof(int32_t) * (size_t)(n_range > n_az ? n_range : n_az));
-    const size_t total = o_st + 256;
+    const size_t o_nr = o_st + 256;
+    const size_t o_na = o_nr + align_up(sizeof(float2) * (size_t)n_range);
+    const size_t total = o_na + align_up(sizeof(float2) * (size_t)n_az);
     cudaError_t e = fault_inject_alloc() ? cudaErrorMemoryAllocation : cudaMalloc(&p->block, total);
     if (e != cudaSuccess) {
         if (e != cudaErrorMemoryAllocation) cudaGetLastError();
@@ -231,6 +234,8 @@ sar_status sar_plan_create_ex(int64_t n_range, int64_t n_az, const sar_filters *
     p->az.tw = (float2 *)(b + o_ta);
     int32_t *idx_dev = (int32_t *)(b + o_ix);
     p->status = (int *)(b + o_st);
+    p->range.filt_nat = (float2 *)(b + o_nr);
+    p->az.filt_nat = (float2 *)(b + o_na);
     p->ctl = sar::FusedCtl{p->status, plan_wait_cycles(), plan_skip_line()};
 
     cudaStream_t s = nullptr;
@@ -262,6 +267,8 @@ sar_status sar_plan_create_ex(int64_t n_range, int64_t n_az, const sar_filters *
             return cleanup_fail(e, "filter index copy");
         if ((e = sar::build_filter(d, (const float2 *)dm.H, dm.lp->filt, idx_dev, s)) != cudaSuccess)
             return cleanup_fail(e, "filter permutation");
+        if ((e = sar::build_natural_filter((const float2 *)dm.H, dm.lp->filt_nat, d.n, s)) != cudaSuccess)
+            return cleanup_fail(e, "natural-order filter");
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cleanup_fail(e, "plan tables");
     }
     cudaStreamDestroy(s);
@@ -516,6 +523,51 @@ sar_status sar_rda_process_oop(sar_plan p, const void *raw, void *work, void *im
     cudaError_t e = sar::launch_transpose((const float2 *)work, (float2 *)image, p->n_az, p->n_range, s);
     if (e != cudaSuccess) return cuda_fail(e, "corner turn launch");
     return run_fused(p, p->az, p->n_range, image, image, s, "azimuth compression launch");
+}
+
+// The unfused comparison path (Sec. II-B, the pipeline the fused kernel
+// replaces): forward FFT kernel, spectrum multiply kernel, inverse FFT
+// kernel, each reading and writing the whole line set (six transfers per
+// line instead of two).
+static sar_status run_unfused(const sar_plan_s *p, const LinePlan &lp, int64_t n_lines, void *data, cudaStream_t s) {
+    const SchedDesc &d = *lp.sched;
+    float2 *tw = nullptr;
+    sar_status st = cached_twiddles(&d, &tw);
+    if (st != SAR_OK) return st;
+    cudaError_t e = d.dft((const float2 *)data, (float2 *)data, n_lines, d.n, d.n, tw, 0, s);
+    if (e == cudaSuccess) e = sar::spectrum_multiply((float2 *)data, lp.filt_nat, n_lines, d.n, s);
+    if (e == cudaSuccess) e = d.dft((const float2 *)data, (float2 *)data, n_lines, d.n, d.n, tw, 1, s);
+    if (e != cudaSuccess) return cuda_fail(e, "unfused pass launch");
+    (void)p;
+    return SAR_OK;
+}
+
+sar_status sar_range_compress_unfused(sar_plan p, void *data, sar_stream stream) {
+    if (!p) return fail(SAR_ERR_INVALID_ARG, "plan is NULL");
+    sar_status st = check_device_ptr(data, "data");
+    if (st != SAR_OK) return st;
+    return run_unfused(p, p->range, p->n_az, data, (cudaStream_t)stream);
+}
+
+sar_status sar_azimuth_compress_unfused(sar_plan p, void *data, sar_stream stream) {
+    if (!p) return fail(SAR_ERR_INVALID_ARG, "plan is NULL");
+    sar_status st = check_device_ptr(data, "data");
+    if (st != SAR_OK) return st;
+    return run_unfused(p, p->az, p->n_range, data, (cudaStream_t)stream);
+}
+
+sar_status sar_rda_process_unfused(sar_plan p, void *raw, void *image, sar_stream stream) {
+    if (!p) return fail(SAR_ERR_INVALID_ARG, "plan is NULL");
+    sar_status st;
+    if ((st = check_device_ptr(raw, "raw")) != SAR_OK) return st;
+    if ((st = check_device_ptr(image, "image")) != SAR_OK) return st;
+    if (overlaps(raw, image, sizeof(float2) * (size_t)(p->n_az * p->n_range)))
+        return fail(SAR_ERR_INVALID_ARG, "raw and image overlap");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = run_unfused(p, p->range, p->n_az, raw, s)) != SAR_OK) return st;
+    cudaError_t e = sar::launch_transpose((const float2 *)raw, (float2 *)image, p->n_az, p->n_range, s);
+    if (e != cudaSuccess) return cuda_fail(e, "corner turn launch");
+    return run_unfused(p, p->az, p->n_range, image, s);
 }
 
 sar_status sar_rda_process_host(sar_plan p, const void *raw, void *image, sar_stream stream) {

@@ -277,14 +277,23 @@ dft_lines_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld,
         for (int j = 0; j < SC::E; ++j) v[j] = cconj(v[j]);
     }
     forward_passes<SC, LPB>(v, sm, tw, t, lib);
-    float2* dst = out + line * SC::N;  // outputs are dense lines of N
+    // natural order through shared memory, then coalesced stores
+    line_sync<SC, LPB>(lib);
 #pragma unroll
     for (int s = 0; s < SC::E / SC::RL; ++s) {
 #pragma unroll
         for (int r = 0; r < SC::RL; ++r) {
-            const float2 x = v[s * SC::RL + r];
-            dst[natural_index<SC>(t + SC::T * s, r)] = INV ? cconj(x) : x;
+            const int k = natural_index<SC>(t + SC::T * s, r);
+            sm[smem_pos(k, SC::PADSH)] = v[s * SC::RL + r];
         }
+    }
+    line_sync<SC, LPB>(lib);
+    float2* dst = out + line * SC::N;  // outputs are dense lines of N
+#pragma unroll
+    for (int j = 0; j < SC::E; ++j) {
+        const int k = t + SC::T * j;
+        const float2 x = sm[smem_pos(k, SC::PADSH)];
+        dst[k] = INV ? cconj(x) : x;
     }
 }
 

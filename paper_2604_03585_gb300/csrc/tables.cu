@@ -49,6 +49,37 @@ __global__ void gather_scale_kernel(float2 *dst, const float2 *H, const int32_t 
     dst[i] = make_float2(h.x * scale, h.y * scale);
 }
 
+// data[l][k] *= h[k] for n_lines lines of n (two samples per thread)
+__global__ void spectrum_multiply_kernel(float4 *data, const float4 *h, int64_t total2, int64_t n2) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total2; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 x = data[i], w = h[i % n2];
+        data[i] = make_float4(fmaf(x.x, w.x, -x.y * w.y), fmaf(x.x, w.y, x.y * w.x), fmaf(x.z, w.z, -x.w * w.w),
+                              fmaf(x.z, w.w, x.w * w.z));
+    }
+}
+
+// dst[k] = H[k] * scale (natural order)
+__global__ void scale_copy_kernel(float2 *dst, const float2 *H, int n, float scale) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = make_float2(H[i].x * scale, H[i].y * scale);
+}
+
+cudaError_t spectrum_multiply(float2 *data, const float2 *h, int64_t n_lines, int64_t n, cudaStream_t st) {
+    const int64_t total2 = n_lines * n / 2;
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t blocks = (total2 + 255) / 256;
+    if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
+    spectrum_multiply_kernel<<<(unsigned)blocks, 256, 0, st>>>((float4 *)data, (const float4 *)h, total2, n / 2);
+    return cudaGetLastError();
+}
+
+cudaError_t build_natural_filter(const float2 *H, float2 *dst, int n, cudaStream_t st) {
+    scale_copy_kernel<<<(n + 255) / 256, 256, 0, st>>>(dst, H, n, 1.0f / (float)n);
+    return cudaGetLastError();
+}
+
 cudaError_t build_twiddles(const SchedDesc &d, float2 *tw, cudaStream_t st) {
     const int S1 = d.n / d.r1;
     int total = d.r1 * S1;

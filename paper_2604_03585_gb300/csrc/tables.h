@@ -7,6 +7,9 @@ cudaError_t build_twiddles(const SchedDesc &d, float2 *tw, cudaStream_t st);
 cudaError_t build_filter(const SchedDesc &d, const float2 *H, float2 *filt, int32_t *idx_dev, cudaStream_t st);
 cudaError_t make_lfm_line(int n, int nc, double tbp, float2 *out, cudaStream_t st);
 cudaError_t conjugate(float2 *x, int n, cudaStream_t st);
+// unfused comparison path: natural-order filter with 1/N, and the multiply
+cudaError_t build_natural_filter(const float2 *H, float2 *dst, int n, cudaStream_t st);
+cudaError_t spectrum_multiply(float2 *data, const float2 *h, int64_t n_lines, int64_t n, cudaStream_t st);
 cudaError_t launch_transpose(const float2 *in, float2 *out, int64_t rows, int64_t cols, cudaStream_t st);
 // 0: automatic (32 x 32 tiles: measured faster on GB300 at 4096^2 and 8192^2),
 // 1: always 32 x 32 tiles, 2: 64 x 64 tiles wherever the shape allows
