@@ -250,6 +250,42 @@ def unfused_bench(sar, plan, raw, work, image, stream, fused_ms: float, reps: in
 
 
 # ---------------------------------------------------------------------------
+# split-precision tensor-core variants on the same scene
+# ---------------------------------------------------------------------------
+
+def precision_bench(sar, Hr, Ha, raw, work, image, stream, reps: int = 50) -> dict:
+    """Time the 4096^2 scene with each split-precision plan (three kernels:
+    range pass, corner turn, azimuth pass) and the FP32 plan through the same
+    unfolded path; the images are compared with the FP32 image here and with
+    the FP64 oracle in tests/test_gpu_parity.py (summarised in profiles/)."""
+    import torch
+    out = {}
+    ref = None
+    for name in ("FP32", "FP16X2", "BF16X2", "BF16X3"):
+        code = getattr(sar, "SAR_PREC_" + name)
+        plan = sar.sar_plan_create(N_RANGE, N_AZ, Hr, Ha, precision=code, flags=sar.SAR_PLAN_UNFOLDED_CORNER_TURN)
+        times = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for i in range(reps + 3):
+            e0.record(stream)
+            sar.sar_rda_process_oop(plan, raw, work, image, stream)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= 3:
+                times.append(e0.elapsed_time(e1))
+        times.sort()
+        img = image.clone()
+        if ref is None:
+            ref = img
+        diff = float(torch.linalg.vector_norm(img - ref) / torch.linalg.vector_norm(ref))
+        out[name] = {"ms_per_scene": times[len(times) // 2], "rel_l2_vs_fp32_path": diff}
+        plan.destroy()
+    out["note"] = ("unfolded three-kernel path for every precision; error against the FP64 oracle: "
+                   "profiles/precision_4096.md")
+    return out
+
+
+# ---------------------------------------------------------------------------
 # ragged batch: 64 strips of mixed sizes in one CUDA-graph launch
 # ---------------------------------------------------------------------------
 
@@ -498,6 +534,7 @@ def main():
     extras = {}
     if not args.no_extras:
         extras["unfused"] = unfused_bench(sar, plan, raws[0], work, image, stream, ms_step)
+        extras["precision"] = precision_bench(sar, Hr, Ha, raws[0], work, image, stream)
         extras["ragged_batch"] = ragged_batch_bench(sar, roofline, dev, stream, peak)
         extras["serving"] = serving_bench(sar, dev, stream)
 

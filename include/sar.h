@@ -61,7 +61,14 @@ typedef enum {
 } sar_status;
 
 typedef enum {
-    SAR_PREC_FP32 = 0 /* FP32 arithmetic throughout (FP64 only for table phases) */
+    SAR_PREC_FP32 = 0,   /* FP32 arithmetic throughout (FP64 only for table phases) */
+    /* Split precision on the tensor cores (Sec. III's MMA DFT, Eq. (1)-(2),
+     * at radix 16): every radix-16 DFT is a real 32 x 32 matrix product of
+     * half-precision parts with FP32 accumulation; twiddles, filter and 1/N
+     * in FP32.  Line lengths 256 and 4096 only; no folded corner turn. */
+    SAR_PREC_FP16X2 = 1, /* x = hi + lo in FP16, products hi*hi + hi*lo + lo*hi, per-group power-of-two scaling */
+    SAR_PREC_BF16X2 = 2, /* the same with BF16 parts (16 mantissa bits in total) */
+    SAR_PREC_BF16X3 = 3  /* BF16 hi + mid + lo, six products (24 mantissa bits) */
 } sar_precision;
 
 /* Matched filters of a plan (Sec. II-B step 3: "pre-computed matched filter").

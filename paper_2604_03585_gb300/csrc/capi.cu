@@ -156,6 +156,7 @@ struct sar_plan_s {
     int device = 0;
     LinePlan range, az;
     int *status = nullptr;  // device word written by timed-out kernels (0 = fine)
+    int prec = SAR_PREC_FP32;
     bool fold = false;      // range pass writes the corner-turned image itself
     sar::FusedCtl ctl{};
     void *block = nullptr;  // one device allocation holding every table
@@ -183,12 +184,17 @@ sar_status sar_plan_create_ex(int64_t n_range, int64_t n_az, const sar_filters *
     if ((st = check_length(n_az, "n_az")) != SAR_OK) return st;
     if (filters->flags & ~SAR_PLAN_UNFOLDED_CORNER_TURN)
         return fail(SAR_ERR_INVALID_ARG, "filters->flags has unknown bits 0x%x", filters->flags);
-    if (filters->precision != SAR_PREC_FP32)
-        return fail(SAR_ERR_UNSUPPORTED, "precision %d is not available", (int)filters->precision);
+    const int prec = filters->precision;
+    if (prec < SAR_PREC_FP32 || prec > SAR_PREC_BF16X3)
+        return fail(SAR_ERR_INVALID_ARG, "unknown precision %d", prec);
+    if (prec != SAR_PREC_FP32 && (!(n_range == 256 || n_range == 4096) || !(n_az == 256 || n_az == 4096)))
+        return fail(SAR_ERR_UNSUPPORTED, "split-precision plans need line lengths 256 or 4096");
+    if (prec != SAR_PREC_FP32 && (range_schedule || az_schedule))
+        return fail(SAR_ERR_INVALID_ARG, "split-precision plans take no schedule names");
     if ((st = check_device_ptr(filters->range_spectrum, "filters->range_spectrum")) != SAR_OK) return st;
     if ((st = check_device_ptr(filters->az_spectrum, "filters->az_spectrum")) != SAR_OK) return st;
 
-    const bool want_fold = !(filters->flags & SAR_PLAN_UNFOLDED_CORNER_TURN);
+    const bool want_fold = !(filters->flags & SAR_PLAN_UNFOLDED_CORNER_TURN) && prec == SAR_PREC_FP32;
     const SchedDesc *dr = range_schedule ? sar::find_schedule(range_schedule) : nullptr;
     if (!range_schedule) {
         dr = want_fold ? sar::default_ct_schedule((int)n_range) : nullptr;
@@ -199,6 +205,11 @@ sar_status sar_plan_create_ex(int64_t n_range, int64_t n_az, const sar_filters *
         return fail(SAR_ERR_INVALID_ARG, "range schedule '%s' is unknown or not for n_range", range_schedule);
     if (az_schedule && (!da || da->n != n_az))
         return fail(SAR_ERR_INVALID_ARG, "azimuth schedule '%s' is unknown or not for n_az", az_schedule);
+    if (prec != SAR_PREC_FP32) {
+        // the tensor-core kernel uses the twiddle tables of the all-radix-16 schedules
+        dr = sar::find_schedule(n_range == 4096 ? "n4096_e32_r16x16x16_sr1" : "n256_e16_r16x16_l8");
+        da = sar::find_schedule(n_az == 4096 ? "n4096_e32_r16x16x16_sr1" : "n256_e16_r16x16_l8");
+    }
     if (!dr || !da) return fail(SAR_ERR_UNSUPPORTED, "no compiled schedule for this size");
 
     sar_plan p = new (std::nothrow) sar_plan_s;
@@ -208,6 +219,7 @@ sar_status sar_plan_create_ex(int64_t n_range, int64_t n_az, const sar_filters *
     cudaGetDevice(&p->device);
     p->range.sched = dr;
     p->az.sched = da;
+    p->prec = prec;
     p->fold = want_fold && dr->fused_ct && n_az % dr->ct_lines == 0;
 
     // one block: filt_r | tw_r | filt_a | tw_a | idx (int32, max n)
@@ -269,6 +281,17 @@ sar_status sar_plan_create_ex(int64_t n_range, int64_t n_az, const sar_filters *
             return cleanup_fail(e, "filter permutation");
         if ((e = sar::build_natural_filter((const float2 *)dm.H, dm.lp->filt_nat, d.n, s)) != cudaSuccess)
             return cleanup_fail(e, "natural-order filter");
+        if (prec != SAR_PREC_FP32) {
+            // position-order filter of the tensor-core kernel, in place of the
+            // register-order one
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cleanup_fail(e, "plan tables");
+            sar::mma_filter_positions(d.n, idx.data());
+            if ((e = cudaMemcpyAsync(idx_dev, idx.data(), sizeof(int32_t) * d.n, cudaMemcpyHostToDevice, s)) !=
+                cudaSuccess)
+                return cleanup_fail(e, "filter index copy");
+            if ((e = sar::build_filter(d, (const float2 *)dm.H, dm.lp->filt, idx_dev, s)) != cudaSuccess)
+                return cleanup_fail(e, "filter permutation");
+        }
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cleanup_fail(e, "plan tables");
     }
     cudaStreamDestroy(s);
@@ -422,6 +445,12 @@ sar_status sar_plan_destroy(sar_plan p) {
 static sar_status run_fused(const sar_plan_s *p, const LinePlan &lp, int64_t n_lines, const void *in, void *out,
                             cudaStream_t s, const char *what) {
     const SchedDesc &d = *lp.sched;
+    if (p->prec != SAR_PREC_FP32) {
+        cudaError_t e = sar::launch_mma_compress(d.n, p->prec, (const float2 *)in, (float2 *)out, n_lines, d.n,
+                                                 lp.filt, lp.tw, s);
+        if (e != cudaSuccess) return cuda_fail(e, what);
+        return SAR_OK;
+    }
     cudaError_t e = d.fused((const float2 *)in, (float2 *)out, n_lines, d.n, d.n, lp.filt, lp.tw, p->ctl, s);
     if (e != cudaSuccess) return cuda_fail(e, what);
     return SAR_OK;

@@ -14,5 +14,9 @@ cudaError_t launch_transpose(const float2 *in, float2 *out, int64_t rows, int64_
 // 0: automatic (32 x 32 tiles: measured faster on GB300 at 4096^2 and 8192^2),
 // 1: always 32 x 32 tiles, 2: 64 x 64 tiles wherever the shape allows
 void set_corner_turn_variant(int v);
+// split-precision tensor-core line compression (N = 256 or 4096)
+cudaError_t launch_mma_compress(int n, int prec, const float2 *in, float2 *out, int64_t n_lines, int64_t ld,
+                                const float2 *filt_pos, const float2 *tw, cudaStream_t st);
+void mma_filter_positions(int n, int32_t *idx);
 int corner_turn_variant();
 }  // namespace sar

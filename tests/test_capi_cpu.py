@@ -48,8 +48,10 @@ def test_argument_errors_without_gpu(sar):
     assert "n_range" in sar.sar_last_error()
     f2 = sar.sar_filters(None, None, 0, 2)
     assert lib.sar_plan_create(256, 256, ctypes.byref(f2), ctypes.byref(h)) == sar.SAR_ERR_INVALID_ARG
-    f3 = sar.sar_filters(None, None, 7, 0)
-    assert lib.sar_plan_create(256, 256, ctypes.byref(f3), ctypes.byref(h)) == sar.SAR_ERR_UNSUPPORTED
+    f3 = sar.sar_filters(None, None, 7, 0)          # unknown precision
+    assert lib.sar_plan_create(256, 256, ctypes.byref(f3), ctypes.byref(h)) == sar.SAR_ERR_INVALID_ARG
+    f4 = sar.sar_filters(None, None, sar.SAR_PREC_FP16X2, 0)   # split precision: 256 / 4096 only
+    assert lib.sar_plan_create(1024, 256, ctypes.byref(f4), ctypes.byref(h)) == sar.SAR_ERR_UNSUPPORTED
     assert h.value is None
     assert lib.sar_fft_lines(100, 1, None, None, 0, None) == sar.SAR_ERR_UNSUPPORTED
     assert lib.sar_fft_lines(256, -1, None, None, 0, None) == sar.SAR_ERR_INVALID_ARG

@@ -492,3 +492,53 @@ def test_allocation_failure_is_reported(sar):
 def test_empty_inputs(sar):
     sar.sar_fft_lines(256, 0, 0, 0)        # zero lines: nothing to do, no pointer needed
     sar.sar_sync()
+
+
+# ---------------------------------------------------------------------------
+# split-precision tensor-core DFTs (precision comparison on the 4096^2 scene)
+# ---------------------------------------------------------------------------
+
+PREC_GATES = {"FP16X2": 2e-5, "BF16X3": 2e-5, "BF16X2": 2e-4}
+
+
+@pytest.mark.parametrize("prec", ["FP16X2", "BF16X2", "BF16X3"])
+@pytest.mark.parametrize("make", [sarsim.scene_256, sarsim.scene_4096], ids=["256", "4096"])
+def test_split_precision_vs_oracle(sar, orc, prec, make):
+    """Error of each split-precision variant against the FP64 oracle, stated
+    for the record (rel-L2, peaks, PSLR/ISLR/SNR deltas); FP16 hi/lo and
+    BF16 hi/mid/lo meet the image gate, BF16 hi/lo is reported with its own
+    (looser) bound."""
+    spec = make()
+    Hr, Ha = gpu_filters(sar, spec)
+    raw = sarsim.echo(spec)
+    code = getattr(sar, "SAR_PREC_" + prec)
+    plan = sar.sar_plan_create(spec.n_range, spec.n_az, Hr, Ha, precision=code)
+    assert not sar.sar_plan_folds_corner_turn(plan)
+    raw_d = dev(raw)
+    img_d = empty_c64(spec.n_range, spec.n_az)
+    sar.sar_rda_process(plan, raw_d, img_d)
+    img = host(img_d)
+    plan.destroy()
+    ref = orc.rda(raw, *oracle_filters(orc, spec), nthreads=NTHREADS)
+    err = M.rel_l2(img, ref)
+    tg = [(r0, a0) for (a0, r0) in spec.targets]
+    qg, qr = M.quality(img, tg), M.quality(ref, tg)
+    worst = {k: max(abs(a[k] - b[k]) for a, b in zip(qg["targets"], qr["targets"]))
+             for k in ("pslr_axis0", "pslr_axis1", "islr_axis0", "islr_axis1", "snr")}
+    print(f"\nPRECISION {prec} {spec.n_az}x{spec.n_range}: rel_l2={err:.3e} max_abs={M.max_abs(img, ref):.3e} "
+          + " ".join(f"d_{k}={v:.4f}dB" for k, v in worst.items()))
+    assert err <= PREC_GATES[prec], err
+    for a, b in zip(qg["targets"], qr["targets"]):
+        assert a["pos"] == b["pos"]
+    if prec != "BF16X2":
+        assert max(worst.values()) <= 0.05
+
+
+def test_split_precision_refusals(sar):
+    x = empty_c64(1024)
+    with pytest.raises(sar.SarError) as e:
+        sar.sar_plan_create(1024, 1024, x, x, precision=sar.SAR_PREC_FP16X2)
+    assert e.value.status == sar.SAR_ERR_UNSUPPORTED
+    with pytest.raises(sar.SarError) as e:
+        sar.sar_plan_create(1024, 1024, x, x, precision=9)
+    assert e.value.status == sar.SAR_ERR_INVALID_ARG
