@@ -61,8 +61,12 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.oracle_compress_lines.argtypes = [i64, i64, vp, vp, c_int]
     lib.oracle_corner_turn.argtypes = [i64, i64, vp, vp]
     lib.oracle_rda.argtypes = [i64, i64, i64, vp, vp, vp, vp, c_int]
+    d = ctypes.c_double
+    lib.oracle_rcmc.argtypes = [i64, i64, vp, vp, d, d, d, c_int]
+    lib.oracle_rda_full.argtypes = [i64, i64, vp, vp, d, d, d, c_int, vp, c_int]
     for name in ("oracle_fft", "oracle_matched_filter", "oracle_compress_line",
-                 "oracle_compress_lines", "oracle_corner_turn", "oracle_rda", "oracle_planted"):
+                 "oracle_compress_lines", "oracle_corner_turn", "oracle_rda", "oracle_planted", "oracle_rcmc",
+                 "oracle_rda_full"):
         getattr(lib, name).restype = c_int
     return lib
 
@@ -143,6 +147,25 @@ class Oracle:
                                    _ptr(img), nthreads), "rda")
         return img
 
+    def rcmc(self, rd, geo, taps: int = 16) -> np.ndarray:
+        """RCMC of range-Doppler data rd[n_range][n_f] (see oracle.c)."""
+        x = _c128(rd)
+        n_range, n_f = x.shape
+        out = np.empty_like(x)
+        _check(self.lib.oracle_rcmc(n_range, n_f, _ptr(x), _ptr(out), *geo.as_tuple(), taps), "rcmc")
+        return out
+
+    def rda_full(self, raw, Hr, geo, taps: int = 16, nthreads: int = 1) -> np.ndarray:
+        """Range compression, corner turn, azimuth FFT, RCMC, range-dependent
+        azimuth filter, azimuth IFFT: raw[n_az][n_range] -> image[n_range][n_az]."""
+        r = _c128(raw)
+        n_az, n_range = r.shape
+        Hr_c = _c128(Hr)
+        img = np.empty((n_range, n_az), np.complex128)
+        _check(self.lib.oracle_rda_full(n_az, n_range, _ptr(r), _ptr(Hr_c), *geo.as_tuple(), taps, _ptr(img),
+                                        nthreads), "rda_full")
+        return img
+
     def planted(self) -> int:
         return int(self.lib.oracle_planted())
 
@@ -175,3 +198,7 @@ def corner_turn(a):
 
 def rda(raw, Hr, Ha, l_az=None, nthreads=1):
     return default().rda(raw, Hr, Ha, l_az, nthreads)
+
+
+def rda_full(raw, Hr, geo, taps=16, nthreads=1):
+    return default().rda_full(raw, Hr, geo, taps, nthreads)

@@ -52,6 +52,7 @@
 typedef double complex cplx;
 
 static const double kTwoPi = 6.283185307179586476925286766559;
+static const double kPi = 3.141592653589793238462643383279;
 
 static int is_pow2(int64_t n) { return n >= 1 && (n & (n - 1)) == 0; }
 
@@ -265,6 +266,116 @@ int oracle_rda(int64_t n_az, int64_t n_range, int64_t l_az, const cplx *raw, con
         memcpy(image + r * n_az, az + r * l_az, sizeof(cplx) * (size_t)n_az);
     free(work);
     free(az);
+    return st ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Full Range-Doppler processing with range cell migration correction        */
+/* (Sec. IV-A steps 2-4: azimuth FFT, RCMC by sinc interpolation, azimuth    */
+/* compression with the range-dependent filter H_a(f_a, R0), azimuth IFFT).  */
+/* ------------------------------------------------------------------------ */
+
+/* Azimuth frequency of spectrum index j of an n-point FFT, cycles per line. */
+static double az_freq(int64_t j, int64_t n) { return (j < n / 2 ? (double)j : (double)(j - n)) / (double)n; }
+
+/* Range-Doppler migration factor D(f) = sqrt(1 - (f / (kappa v_s))^2): in the
+ * range-Doppler domain a target of closest range r0 sits at range r0 / D(f). */
+static double migration_d(double f, double kappa, double vs)
+{
+    double q = f / (kappa * vs);
+    return sqrt(1.0 - q * q);
+}
+
+/* Interpolation kernel of the RCMC: a sinc of `taps` samples (taps even)
+ * under a Hann window, h(x) = sinc(x) * 0.5 (1 + cos(2 pi x / taps)) for
+ * |x| < taps / 2, else 0; sinc(x) = sin(pi x) / (pi x). */
+static double rcmc_kernel(double x, int taps)
+{
+    if (fabs(x) >= taps / 2.0)
+        return 0.0;
+    double s = (x == 0.0) ? 1.0 : sin(kPi * x) / (kPi * x);
+    return s * 0.5 * (1.0 + cos(kTwoPi * x / (double)taps));
+}
+
+/* RCMC on the range-Doppler data rd[n_range][n_f] (row: range bin, column:
+ * azimuth frequency index).  Output bin n at frequency f reads the input at
+ * the migrated range n + (r_near + n)(1/D(f) - 1), interpolated with
+ * rcmc_kernel over the taps nearest to it; samples outside the range extent
+ * count as zero.  taps = 0 copies the data (no correction). */
+int oracle_rcmc(int64_t n_range, int64_t n_f, const cplx *rd, cplx *out, double kappa, double vs, double r_near,
+                int taps)
+{
+    if (n_range < 1 || n_f < 1 || !rd || !out || taps < 0 || (taps & 1))
+        return -1;
+    for (int64_t j = 0; j < n_f; ++j) {
+        double d = migration_d(az_freq(j, n_f), kappa, vs);
+        for (int64_t n = 0; n < n_range; ++n) {
+            if (taps == 0) {
+                out[n * n_f + j] = rd[n * n_f + j];
+                continue;
+            }
+            double src = (double)n + (r_near + (double)n) * (1.0 / d - 1.0);
+            int64_t k0 = (int64_t)floor(src);
+            cplx acc = 0.0;
+            for (int64_t k = k0 - taps / 2 + 1; k <= k0 + taps / 2; ++k) {
+                if (k < 0 || k >= n_range)
+                    continue;
+                acc += rcmc_kernel(src - (double)k, taps) * rd[k * n_f + j];
+            }
+#if ORACLE_PLANT == 7
+            acc = rd[n * n_f + j]; /* planted: no correction */
+#endif
+            out[n * n_f + j] = acc;
+        }
+    }
+    return 0;
+}
+
+/* The whole processor: raw[n_az][n_range] -> image[n_range][n_az].
+ * 1. range compression with Hr (per azimuth line, as oracle_rda);
+ * 2. corner turn; 3. azimuth FFT per range bin;
+ * 4. RCMC (oracle_rcmc);
+ * 5. azimuth compression: multiply by H_a(f, r) = exp(+2 pi i kappa r D(f)),
+ *    r = r_near + n, which cancels the target phase exp(-2 pi i kappa r0 D(f))
+ *    of the stationary-phase spectrum, and the azimuth IFFT (1/n_az).
+ * n_range, n_az powers of two. */
+int oracle_rda_full(int64_t n_az, int64_t n_range, const cplx *raw, const cplx *Hr, double kappa, double vs,
+                    double r_near, int taps, cplx *image, int nthreads)
+{
+    if (!is_pow2(n_az) || !is_pow2(n_range) || !raw || !Hr || !image)
+        return -1;
+    size_t total = (size_t)(n_az * n_range);
+    cplx *work = (cplx *)malloc(sizeof(cplx) * total);
+    cplx *rd = (cplx *)malloc(sizeof(cplx) * total);
+    if (!work || !rd) {
+        free(work);
+        free(rd);
+        return -1;
+    }
+    int st = 0;
+    memcpy(work, raw, sizeof(cplx) * total);
+    st |= oracle_compress_lines(n_az, n_range, work, Hr, nthreads);
+    st |= oracle_corner_turn(n_az, n_range, work, rd);                 /* rd[n][m] */
+    for (int64_t n = 0; n < n_range; ++n)
+        st |= oracle_fft(n_az, rd + n * n_az, -1);                      /* rd[n][f] */
+    st |= oracle_rcmc(n_range, n_az, rd, image, kappa, vs, r_near, taps);
+    for (int64_t n = 0; n < n_range; ++n) {
+        double r = r_near + (double)n;
+        cplx *line = image + n * n_az;
+        for (int64_t j = 0; j < n_az; ++j) {
+            double cyc = kappa * r * migration_d(az_freq(j, n_az), kappa, vs);
+            double ph = kTwoPi * (cyc - floor(cyc));
+#if ORACLE_PLANT == 8
+            ph = -ph; /* planted: filter conjugated */
+#endif
+            line[j] *= cos(ph) + I * sin(ph);
+        }
+        st |= oracle_fft(n_az, line, +1);
+        for (int64_t j = 0; j < n_az; ++j)
+            line[j] /= (double)n_az;
+    }
+    free(work);
+    free(rd);
     return st ? -1 : 0;
 }
 

@@ -264,3 +264,51 @@ def serving_scene(size: int, variant: int, seed: int = 5) -> SceneSpec:
     tg = place_targets(s, size, size, n_t, margin_az=ac[0] // 2 + 1, margin_r=rc[0] // 2 + 1,
                        min_sep=min(256, size // 32))
     return SceneSpec(size, size, tg, rc, ac, 10.0, s)
+
+
+# ---------------------------------------------------------------------------
+# Range-migration scenes (full Range-Doppler processing with RCMC).
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Geometry:
+    """Normalised side-looking geometry, in range samples and azimuth lines.
+
+    kappa:  two-way phase in cycles per range sample of path (2 dr / lambda);
+    v_s:    platform displacement per azimuth line, in range samples;
+    r_near: slant range of range bin 0, in range samples.
+    A target at range bin n0 and azimuth line a0 has closest range
+    r0 = r_near + n0 and range history r(m) = sqrt(r0^2 + v_s^2 (m - a0)^2);
+    its azimuth chirp rate is kappa v_s^2 / r0 cycles per line^2."""
+    kappa: float = 10.0
+    v_s: float = 0.3
+    r_near: float = 4000.0
+
+    def as_tuple(self):
+        return (self.kappa, self.v_s, self.r_near)
+
+
+def echo_migration(n_az: int, n_range: int, targets: list, range_chirp: tuple, aperture: int, geo: Geometry,
+                   snr_db: float | None, seed: int, dtype=np.complex64) -> np.ndarray:
+    """Raw echo with range migration: target (a0, n0) contributes, on each
+    azimuth line m with |m - a0| < aperture/2, the range chirp delayed to the
+    fractional range r(m) - r_near,
+        exp(i pi K (n - (r(m) - r_near))^2)  for |n - (r(m) - r_near)| < n_c/2,
+    times the two-way phase exp(-2 pi i kappa r(m)).  Lines and range samples
+    do not wrap.  Noise as in `echo`."""
+    n_c, tbp = range_chirp
+    K = tbp / (n_c * n_c)
+    sig = np.zeros((n_az, n_range), np.complex128)
+    n = np.arange(n_range, dtype=np.float64)
+    for (a0, n0) in targets:
+        r0 = geo.r_near + n0
+        for m in range(max(0, a0 - aperture // 2), min(n_az, a0 + aperture - aperture // 2)):
+            r = np.sqrt(r0 * r0 + (geo.v_s * (m - a0)) ** 2)
+            t = n - (r - geo.r_near)
+            on = (t >= -(n_c // 2)) & (t < n_c - n_c // 2)
+            cyc = np.fmod(geo.kappa * r, 1.0)
+            sig[m, on] += np.exp(1j * np.pi * K * t[on] * t[on]) * np.exp(-2j * np.pi * cyc)
+    if snr_db is not None:
+        var = 10.0 ** (-snr_db / 10.0)
+        sig += complex_gaussian(seed, STREAM_NOISE, n_az * n_range, var).reshape(n_az, n_range).astype(np.complex128)
+    return sig.astype(dtype)

@@ -16,6 +16,11 @@ What pins what:
                         (Sec. IV-A steps 1-4 as one formula); exact
                         point-target peak value n_ca*n_cr at the planted
                         position; impulse response in closed form.
+* rcmc               -- band-limited exponentials shifted by the analytic
+                        fractional migration; zero Doppler unchanged.
+* rda_full           -- a migrating point target focuses at its planted
+                        position with the closed-form phase-only gain
+                        N_cr sqrt(K_a) T, and not without RCMC.
 * quality metrics    -- Dirichlet kernel (sampled sinc) closed form
                         PSLR -13.26 dB / ISLR -9.68 dB; unweighted LFM at
                         TBP >= 128 within 0.15 dB of it; low-TBP LFM against
@@ -192,9 +197,55 @@ def pin_impulse_response(o):
     assert np.max(np.abs(img - ref)) < 1e-13
 
 
+GEO_PIN = sarsim.Geometry(kappa=10.0, v_s=0.6, r_near=2000.0)   # ~6 range cells of migration
+
+
+def pin_rcmc_bandlimited_shift(o):
+    """RCMC moves each range-Doppler column by the fractional migration;
+    on band-limited exponentials exp(2 pi i nu k) the Hann-windowed sinc must
+    reproduce the analytic value at the fractional source position (within
+    the passband ripple of a 16-tap Hann-windowed sinc, which grows with the
+    frequency), and the zero-Doppler column (no migration) must come out
+    unchanged up to the rounding of sin(pi t) at integers."""
+    geo = GEO_PIN
+    n_range, n_f = 256, 64
+    j = np.arange(n_f)
+    f = np.where(j < n_f // 2, j, j - n_f) / n_f
+    D = np.sqrt(1 - (f / (geo.kappa * geo.v_s)) ** 2)
+    n = np.arange(n_range)[:, None]
+    for nu, tol in ((0.05, 1e-3), (-0.2, 2e-3), (0.3, 5e-3)):
+        rd = np.exp(2j * np.pi * nu * n) * np.ones((1, n_f))
+        out = o.rcmc(rd, geo, taps=16)
+        src = n + (geo.r_near + n) * (1.0 / D[None, :] - 1.0)
+        exact = np.exp(2j * np.pi * nu * src)
+        inside = (src >= 10) & (src < n_range - 10)
+        assert np.max(np.abs(out - exact)[inside]) < tol, nu
+        assert np.max(np.abs(out[:, 0] - rd[:, 0])) < 1e-14
+    assert np.max(src - n) > 5.0          # the migration spans several range cells
+
+
+def pin_rda_full_point_target(o):
+    """A point target with range migration focuses at its planted position
+    with the closed-form gain of the phase-only azimuth filter,
+    N_cr * sqrt(K_a) * T (K_a = kappa v_s^2 / r0, T the aperture in lines),
+    and RCMC is what makes it focus (without it the peak drops)."""
+    geo = GEO_PIN
+    n_az, n_r, ap = 1024, 256, 512
+    a0, n0 = 500, 100
+    raw = sarsim.echo_migration(n_az, n_r, [(a0, n0)], (64, 32.0), ap, geo, None, 1, np.complex128)
+    Hr = o.matched_filter(n_r, sarsim.lfm_chirp(64, 32.0))
+    img = o.rda_full(raw, Hr, geo, taps=16, nthreads=4)
+    ka = geo.kappa * geo.v_s ** 2 / (geo.r_near + n0)
+    ideal = 64 * np.sqrt(ka) * ap
+    assert M.peak(img, (n0, a0)) == (n0, a0)
+    assert abs(abs(img[n0, a0]) / ideal - 1.0) < 0.06, abs(img[n0, a0]) / ideal
+    plain = o.rda_full(raw, Hr, geo, taps=0, nthreads=4)
+    assert abs(plain).max() < 0.8 * abs(img[n0, a0])
+
+
 ALL_PINS = [pin_fft_numpy, pin_fft_dft_matrix, pin_fft_identities, pin_matched_filter,
             pin_compress_lines_circulant, pin_corner_turn, pin_rda_bruteforce,
-            pin_point_target_peaks, pin_impulse_response]
+            pin_point_target_peaks, pin_impulse_response, pin_rcmc_bandlimited_shift, pin_rda_full_point_target]
 
 
 @pytest.mark.parametrize("pin", ALL_PINS, ids=lambda f: f.__name__)
@@ -269,7 +320,7 @@ def test_rel_l2_and_peak_tiebreak():
 # planted mistakes: every deliberately broken oracle must fail a pin
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("plant", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("plant", [1, 2, 3, 4, 5, 6, 7, 8])
 def test_planted_mistake_is_caught(plant, tmp_path):
     path = oracle.build(str(tmp_path / f"liboracle_plant{plant}.so"), plant=plant, force=True)
     o = oracle.Oracle(oracle.load(path))
