@@ -159,6 +159,27 @@ SAR_API sar_status sar_range_compress_unfused(sar_plan plan, void *data, sar_str
 SAR_API sar_status sar_azimuth_compress_unfused(sar_plan plan, void *data, sar_stream stream);
 SAR_API sar_status sar_rda_process_unfused(sar_plan plan, void *raw, void *image, sar_stream stream);
 
+/* ---- full Range-Doppler processing with RCMC (Sec. IV-A steps 2-4) ----
+ * Geometry, in normalised units: kappa = two-way phase cycles per range
+ * sample of path (2 dr / lambda); v_s = platform displacement per azimuth line
+ * in range samples; r_near = slant range of range bin 0 in range samples.  A
+ * target of closest range r0 sits, in the range-Doppler domain, at range
+ * r0 / D(f) with D(f) = sqrt(1 - (f / (kappa v_s))^2) (f in cycles per line)
+ * and carries the phase exp(-2 pi i kappa r0 D(f)).  kappa * v_s > 0.5.
+ * rcmc_taps: 16 (Hann-windowed sinc interpolation) or 0 (no correction).
+ * Stores a per-frequency table in the plan (FP64 evaluated, FP32 stored). */
+SAR_API sar_status sar_plan_set_geometry(sar_plan plan, double kappa, double v_s, double r_near, int32_t rcmc_taps);
+
+/* The full processor: range compression and corner turn (raw -> image),
+ * azimuth FFT of every range bin (in place), RCMC (image -> work: output bin n
+ * at frequency f interpolates the input at n + (r_near + n)(1/D(f) - 1)), and
+ * azimuth compression (work -> image): multiply by
+ * H_a(f, r) = exp(+2 pi i kappa r D(f)), r = r_near + n, then the inverse FFT
+ * (1/n_az).  raw: device complex64[n_az][n_range] (read only); work, image:
+ * device complex64[n_range][n_az]; no overlaps.  The first call per line
+ * length allocates the library's twiddle tables. */
+SAR_API sar_status sar_rda_full(sar_plan plan, const void *raw, void *work, void *image, sar_stream stream);
+
 /* The same three steps on HOST buffers: copies raw to the device, runs
  * sar_rda_process, copies the image back, and returns once the image is in
  * host memory.  raw: host complex64[n_az][n_range] (not modified);

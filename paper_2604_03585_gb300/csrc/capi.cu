@@ -162,6 +162,10 @@ struct sar_plan_s {
     void *block = nullptr;  // one device allocation holding every table
     std::mutex host_mu;
     void *stage_raw = nullptr, *stage_img = nullptr;  // lazily, for the host-buffer entry point
+    // full Range-Doppler processing (sar_plan_set_geometry)
+    void *rd_cols = nullptr;
+    double kappa = 0, vs = 0, r_near = 0;
+    int taps = 0;
 };
 
 extern "C" {
@@ -438,6 +442,7 @@ sar_status sar_plan_destroy(sar_plan p) {
     cudaFree(p->block);
     if (p->stage_raw) cudaFree(p->stage_raw);
     if (p->stage_img) cudaFree(p->stage_img);
+    if (p->rd_cols) cudaFree(p->rd_cols);
     delete p;
     return SAR_OK;
 }
@@ -537,6 +542,23 @@ sar_status sar_range_compress_ct(sar_plan p, const void *raw, void *image, sar_s
     return SAR_OK;
 }
 
+// Range compression and corner turn raw -> image (work as scratch when the
+// corner turn is not folded).
+static sar_status sar_rda_process_oop_range(sar_plan p, const void *raw, void *work, void *image, cudaStream_t s) {
+    if (p->fold) {
+        const SchedDesc &d = *p->range.sched;
+        cudaError_t e = d.fused_ct((const float2 *)raw, (float2 *)image, p->n_az, p->n_range, p->n_az, p->range.filt,
+                                   p->range.tw, s);
+        if (e != cudaSuccess) return cuda_fail(e, "range compression + corner turn launch");
+        return SAR_OK;
+    }
+    sar_status st = run_fused(p, p->range, p->n_az, raw, work, s, "range compression launch");
+    if (st != SAR_OK) return st;
+    cudaError_t e = sar::launch_transpose((const float2 *)work, (float2 *)image, p->n_az, p->n_range, s);
+    if (e != cudaSuccess) return cuda_fail(e, "corner turn launch");
+    return SAR_OK;
+}
+
 sar_status sar_rda_process_oop(sar_plan p, const void *raw, void *work, void *image, sar_stream stream) {
     if (!p) return fail(SAR_ERR_INVALID_ARG, "plan is NULL");
     sar_status st;
@@ -597,6 +619,67 @@ sar_status sar_rda_process_unfused(sar_plan p, void *raw, void *image, sar_strea
     cudaError_t e = sar::launch_transpose((const float2 *)raw, (float2 *)image, p->n_az, p->n_range, s);
     if (e != cudaSuccess) return cuda_fail(e, "corner turn launch");
     return run_unfused(p, p->az, p->n_range, image, s);
+}
+
+sar_status sar_plan_set_geometry(sar_plan p, double kappa, double v_s, double r_near, int32_t rcmc_taps) {
+    if (!p) return fail(SAR_ERR_INVALID_ARG, "plan is NULL");
+    if (!(kappa > 0) || !(v_s > 0) || !(r_near >= 0))
+        return fail(SAR_ERR_INVALID_ARG, "kappa, v_s must be > 0 and r_near >= 0");
+    if (kappa * v_s <= 0.5)
+        return fail(SAR_ERR_INVALID_ARG, "kappa * v_s must exceed 0.5 (every azimuth frequency must migrate)");
+    if (rcmc_taps != 0 && rcmc_taps != 16) return fail(SAR_ERR_UNSUPPORTED, "rcmc_taps must be 0 or 16");
+    if (p->prec != SAR_PREC_FP32) return fail(SAR_ERR_UNSUPPORTED, "full processing runs in FP32 only");
+    std::vector<unsigned char> host(sar::rd_column_bytes() * (size_t)p->n_az);
+    sar::rd_columns((int)p->n_az, kappa, v_s, host.data());
+    if (!p->rd_cols) {
+        if (cudaMalloc(&p->rd_cols, host.size()) != cudaSuccess) {
+            cudaGetLastError();
+            p->rd_cols = nullptr;
+            return fail(SAR_ERR_OUT_OF_MEMORY, "geometry table");
+        }
+    }
+    SAR_CUDA(cudaMemcpy(p->rd_cols, host.data(), host.size(), cudaMemcpyHostToDevice), "geometry table copy");
+    p->kappa = kappa;
+    p->vs = v_s;
+    p->r_near = r_near;
+    p->taps = rcmc_taps;
+    return SAR_OK;
+}
+
+sar_status sar_rda_full(sar_plan p, const void *raw, void *work, void *image, sar_stream stream) {
+    if (!p) return fail(SAR_ERR_INVALID_ARG, "plan is NULL");
+    if (!p->rd_cols) return fail(SAR_ERR_INVALID_ARG, "the plan has no geometry (sar_plan_set_geometry)");
+    sar_status st;
+    if ((st = check_device_ptr(raw, "raw")) != SAR_OK) return st;
+    if ((st = check_device_ptr(work, "work")) != SAR_OK) return st;
+    if ((st = check_device_ptr(image, "image")) != SAR_OK) return st;
+    const size_t bytes = sizeof(float2) * (size_t)(p->n_az * p->n_range);
+    if (overlaps(raw, work, bytes) || overlaps(raw, image, bytes) || overlaps(work, image, bytes))
+        return fail(SAR_ERR_INVALID_ARG, "raw, work and image must not overlap");
+    cudaStream_t s = (cudaStream_t)stream;
+    // 1. range compression and corner turn: raw -> image [n_range][n_az]
+    if ((st = sar_rda_process_oop_range(p, raw, work, image, s)) != SAR_OK) return st;
+    // 2. azimuth FFT of every range bin, in place
+    const SchedDesc &da = *p->az.sched;
+    float2 *tw_fft = nullptr, *tw_az = nullptr;
+    if ((st = cached_twiddles(&da, &tw_fft)) != SAR_OK) return st;
+    const SchedDesc *dz = sar::find_schedule(sar::rd_az_schedule((int)p->n_az));
+    if (!dz) return fail(SAR_ERR_UNSUPPORTED, "no azimuth schedule for this length");
+    if ((st = cached_twiddles(dz, &tw_az)) != SAR_OK) return st;
+    cudaError_t e = da.dft((const float2 *)image, (float2 *)image, p->n_range, p->n_az, (int)p->n_az, tw_fft, 0, s);
+    if (e != cudaSuccess) return cuda_fail(e, "azimuth FFT launch");
+    // 3. RCMC image -> work (or no correction: work <- image)
+    if (p->taps)
+        e = sar::launch_rcmc(p->taps, (const float2 *)image, (float2 *)work, (int)p->n_range, (int)p->n_az, p->rd_cols,
+                             p->r_near, s);
+    else
+        e = cudaMemcpyAsync(work, image, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "RCMC launch");
+    // 4. azimuth compression with the range-dependent filter and IFFT: work -> image
+    e = sar::launch_az_compress_rd((int)p->n_az, (const float2 *)work, (float2 *)image, p->n_range, tw_az, p->rd_cols,
+                                   p->r_near, s);
+    if (e != cudaSuccess) return cuda_fail(e, "azimuth compression launch");
+    return SAR_OK;
 }
 
 sar_status sar_rda_process_host(sar_plan p, const void *raw, void *image, sar_stream stream) {

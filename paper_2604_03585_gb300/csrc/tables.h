@@ -18,5 +18,13 @@ void set_corner_turn_variant(int v);
 cudaError_t launch_mma_compress(int n, int prec, const float2 *in, float2 *out, int64_t n_lines, int64_t ld,
                                 const float2 *filt_pos, const float2 *tw, cudaStream_t st);
 void mma_filter_positions(int n, int32_t *idx);
+// full Range-Doppler processing (RCMC and the range-dependent azimuth filter)
+const char *rd_az_schedule(int n);
+cudaError_t launch_az_compress_rd(int n, const float2 *in, float2 *out, int64_t n_lines, const float2 *tw,
+                                  const void *cols, double r_near, cudaStream_t st);
+cudaError_t launch_rcmc(int taps, const float2 *in, float2 *out, int n_range, int n_f, const void *cols,
+                        double r_near, cudaStream_t st);
+void rd_columns(int n_f, double kappa, double vs, void *host_cols);
+size_t rd_column_bytes();
 int corner_turn_variant();
 }  // namespace sar

@@ -312,3 +312,13 @@ def echo_migration(n_az: int, n_range: int, targets: list, range_chirp: tuple, a
         var = 10.0 ** (-snr_db / 10.0)
         sig += complex_gaussian(seed, STREAM_NOISE, n_az * n_range, var).reshape(n_az, n_range).astype(np.complex128)
     return sig.astype(dtype)
+
+
+def migration_scene_4096(seed: int = 2):
+    """The 4096 x 4096 scene of the full processor: the five targets of
+    scene_4096 (range bins and lines), range LFM 512 / TBP 256, synthetic
+    aperture 1024 lines, geometry kappa 10, v_s 0.3, r_near 4000 (about 3.5
+    range cells of migration at the aperture edges), 10 dB SNR.  Returns
+    (targets, range_chirp, aperture, geometry, snr_db, seed)."""
+    base = scene_4096(seed)
+    return base.targets, (512, 256.0), 1024, Geometry(10.0, 0.3, 4000.0), 10.0, seed
