@@ -170,6 +170,15 @@ SAR_API sar_status sar_rda_process_unfused(sar_plan plan, void *raw, void *image
  * Stores a per-frequency table in the plan (FP64 evaluated, FP32 stored). */
 SAR_API sar_status sar_plan_set_geometry(sar_plan plan, double kappa, double v_s, double r_near, int32_t rcmc_taps);
 
+/* RCMC alone (Sec. IV-A step 2, sinc interpolation), in the range-Doppler
+ * domain: out[n][j] = sum over the 16 integers k nearest
+ * src = n + (r_near + n)(1/D(f_j) - 1) of h(src - k) in[k][j], with
+ * h(x) = sinc(x) (1 + cos(2 pi x / 16)) / 2 and rows outside the scene read as
+ * zero; f_j = j / n_az for j < n_az / 2, (j - n_az) / n_az above.  in, out:
+ * device complex64[n_range][n_az], not overlapping.  Needs a geometry with
+ * rcmc_taps = 16 (SAR_ERR_INVALID_ARG otherwise). */
+SAR_API sar_status sar_rcmc(sar_plan plan, const void *in, void *out, sar_stream stream);
+
 /* The full processor: range compression and corner turn (raw -> image),
  * azimuth FFT of every range bin (in place), RCMC (image -> work: output bin n
  * at frequency f interpolates the input at n + (r_near + n)(1/D(f) - 1)), and

@@ -37,7 +37,7 @@ STATUS_NAMES = {0: "SAR_OK", 1: "SAR_ERR_INVALID_ARG", 2: "SAR_ERR_UNSUPPORTED",
 EXPORTS = ("sar_plan_create", "sar_plan_destroy", "sar_range_compress", "sar_corner_turn",
            "sar_azimuth_compress", "sar_rda_process", "sar_range_compress_oop", "sar_range_compress_ct", "sar_rda_process_oop",
            "sar_range_compress_unfused", "sar_azimuth_compress_unfused", "sar_rda_process_unfused",
-           "sar_plan_set_geometry", "sar_rda_full",
+           "sar_plan_set_geometry", "sar_rcmc", "sar_rda_full",
            "sar_rda_process_host", "sar_make_lfm_spectrum", "sar_simulate_echo",
            "sar_fft_lines", "sar_fft_lines_static", "sar_transpose", "sar_schedule_count", "sar_schedule_get",
            "sar_set_preferred_schedule", "sar_set_corner_turn_variant", "sar_plan_create_ex", "sar_plan_get_schedules", "sar_plan_folds_corner_turn", "sar_autotune",
@@ -103,6 +103,7 @@ _SIGS = {
     "sar_azimuth_compress_unfused": [_vp, _vp, _vp],
     "sar_rda_process_unfused": [_vp, _vp, _vp, _vp],
     "sar_plan_set_geometry": [_vp, _dbl, _dbl, _dbl, ctypes.c_int32],
+    "sar_rcmc": [_vp, _vp, _vp, _vp],
     "sar_rda_full": [_vp, _vp, _vp, _vp, _vp],
     "sar_rda_process_oop": [_vp, _vp, _vp, _vp, _vp],
     "sar_rda_process_host": [_vp, _vp, _vp, _vp],
@@ -319,6 +320,10 @@ def sar_rda_process_unfused(plan, raw, image, stream=None) -> None:
 
 def sar_plan_set_geometry(plan, kappa: float, v_s: float, r_near: float, rcmc_taps: int = 16) -> None:
     _check(_lib.sar_plan_set_geometry(_h(plan), float(kappa), float(v_s), float(r_near), int(rcmc_taps)))
+
+
+def sar_rcmc(plan, data_in, data_out, stream=None) -> None:
+    _check(_lib.sar_rcmc(_h(plan), _ptr(data_in), _ptr(data_out), _stream(stream)))
 
 
 def sar_rda_full(plan, raw, work, image, stream=None) -> None:

@@ -166,6 +166,7 @@ struct sar_plan_s {
     void *rd_cols = nullptr;
     double kappa = 0, vs = 0, r_near = 0;
     int taps = 0;
+    int rcmc_rows = 0;   // input rows one RCMC tile stages in shared memory
 };
 
 extern "C" {
@@ -643,6 +644,22 @@ sar_status sar_plan_set_geometry(sar_plan p, double kappa, double v_s, double r_
     p->vs = v_s;
     p->r_near = r_near;
     p->taps = rcmc_taps;
+    p->rcmc_rows = sar::rcmc_staged_rows((int)p->n_range, (int)p->n_az, r_near, host.data());
+    return SAR_OK;
+}
+
+sar_status sar_rcmc(sar_plan p, const void *in, void *out, sar_stream stream) {
+    if (!p) return fail(SAR_ERR_INVALID_ARG, "plan is NULL");
+    if (!p->rd_cols || p->taps != 16)
+        return fail(SAR_ERR_INVALID_ARG, "the plan has no geometry with 16 RCMC taps (sar_plan_set_geometry)");
+    sar_status st;
+    if ((st = check_device_ptr(in, "in")) != SAR_OK) return st;
+    if ((st = check_device_ptr(out, "out")) != SAR_OK) return st;
+    const size_t bytes = sizeof(float2) * (size_t)(p->n_az * p->n_range);
+    if (overlaps(in, out, bytes)) return fail(SAR_ERR_INVALID_ARG, "in and out must not overlap");
+    cudaError_t e = sar::launch_rcmc(16, (const float2 *)in, (float2 *)out, (int)p->n_range, (int)p->n_az,
+                                     p->rd_cols, p->r_near, p->rcmc_rows, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "RCMC launch");
     return SAR_OK;
 }
 
@@ -671,7 +688,7 @@ sar_status sar_rda_full(sar_plan p, const void *raw, void *work, void *image, sa
     // 3. RCMC image -> work (or no correction: work <- image)
     if (p->taps)
         e = sar::launch_rcmc(p->taps, (const float2 *)image, (float2 *)work, (int)p->n_range, (int)p->n_az, p->rd_cols,
-                             p->r_near, s);
+                             p->r_near, p->rcmc_rows, s);
     else
         e = cudaMemcpyAsync(work, image, bytes, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "RCMC launch");

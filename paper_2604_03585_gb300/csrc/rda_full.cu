@@ -38,49 +38,147 @@ __constant__ float2 kHann16[16] = {SAR_RC(-7), SAR_RC(-6), SAR_RC(-5), SAR_RC(-4
                                    SAR_RC(5),  SAR_RC(6),  SAR_RC(7),  SAR_RC(8)};
 #undef SAR_RC
 
-// RCMC, one output sample per thread: out[n][j] = sum_t h(src - k_t) in[k_t][j],
-// src = n + (r_near + n)(1/D(f_j) - 1), k_t the 16 integers nearest src,
-// h(x) = sinc(x) * 0.5 (1 + cos(2 pi x / 16)).
-template <int TAPS>
-__global__ void __launch_bounds__(256)
-rcmc_kernel(const float2* __restrict__ in, float2* __restrict__ out, int n_range, int n_f, const RdColumn* cols,
-            double r_near) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)n_range * n_f) return;
-    const int n = (int)(idx / n_f), j = (int)(idx % n_f);
-    const double rd = r_near + (double)n;
-    const float r_hi = (float)rd, r_lo = (float)(rd - (double)r_hi);
-    const RdColumn c = cols[j];
-    // shift = r (mig_hi + mig_lo) = p + e + ..., p the rounded product, e its exact error
-    const float p = r_hi * c.mig_hi;
-    const float e = fmaf(r_hi, c.mig_hi, -p);
+// RCMC tiles: 32 frequency columns (one per lane) x 128 range bins per block of
+// 8 warps.  A block stages the input rows its outputs touch in shared memory
+// (rows n0 + min shift - 7 ... n0 + 127 + max shift + 8, zero outside the
+// scene); the host sizes that span from the geometry, and a block whose span
+// does not fit reads global memory directly.
+constexpr int kRcCols = 32;
+constexpr int kRcRows = 128;
+constexpr int kRcWarps = 8;
+constexpr int kRcMaxStaged = 384;   // 96 KB of staged rows per block
+
+// Source position of output bin n in column c: k0 + frac, frac in [0, 1), for
+// r = r_near + n with r_near = rn_hi + rn_lo.  r is formed by a two-sum and the
+// shift r (1/D - 1) by a two-product, so only the fractional part is rounded.
+__device__ __forceinline__ void rc_locate(int n, const RdColumn& c, float rn_hi, float rn_lo, int& k0, float& frac) {
+    const float nf = (float)n;
+    const float r_hi = rn_hi + nf;                       // two-sum of rn_hi and n
+    const float bb = r_hi - rn_hi;
+    const float r_lo = ((rn_hi - (r_hi - bb)) + (nf - bb)) + rn_lo;
+    const float p = __fmul_rn(r_hi, c.mig_hi);            // never contracted into the next subtraction
+    const float e = fmaf(r_hi, c.mig_hi, -p);             // exact error of the product
     const float fl = floorf(p);
-    float frac = (p - fl) + (e + fmaf(r_hi, c.mig_lo, r_lo * c.mig_hi));   // p - fl is exact
-    int k0 = n + (int)fl;
+    frac = (p - fl) + (e + fmaf(r_hi, c.mig_lo, r_lo * c.mig_hi));   // p - fl is exact
+    k0 = n + (int)fl;
     if (frac < 0.f) { frac += 1.f; k0 -= 1; }
     if (frac >= 1.f) { frac -= 1.f; k0 += 1; }
-    float s0, c0, sw, cw;
-    sincospif(frac, &s0, &c0);
-    sincospif(frac * (2.0f / TAPS), &sw, &cw);
+}
+
+__device__ __forceinline__ float rc_rcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// (cw, sw) = (cos, sin)(pi frac / 8) and s = sin(pi frac) for frac in (0, 1),
+// each to a few FP32 ulps, s relative to its own size near frac = 0 and 1.
+// With g = min(frac, 1 - frac) <= 1/2 and theta = pi g / 8 <= pi / 16, sin and
+// cos of theta come from their Taylor series (the first omitted terms are below
+// 2e-12), s = sin(pi g) = sin(8 theta) from three angle doublings in which
+// every cosine stays >= cos(pi / 4) (no cancellation), and for frac > 1/2 the
+// window angle is pi / 8 - theta.
+__device__ __forceinline__ void rc_trig(float frac, float& cw, float& sw, float& s) {
+    const bool flip = frac > 0.5f;
+    const float g = flip ? 1.f - frac : frac;   // exact
+    const float th = g * 0.392699081698724155f;  // pi / 8
+    const float t2 = th * th;
+    const float s8 = th * fmaf(t2, fmaf(t2, fmaf(t2, -1.f / 5040.f, 1.f / 120.f), -1.f / 6.f), 1.f);
+    const float c8 = fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, 1.f / 40320.f, -1.f / 720.f), 1.f / 24.f), -0.5f), 1.f);
+    float a = 2.f * s8;
+    const float s4 = a * c8, c4 = fmaf(-a, s8, 1.f);   // pi g / 4
+    a = 2.f * s4;
+    const float s2 = a * c4, c2 = fmaf(-a, s4, 1.f);   // pi g / 2
+    s = 2.f * s2 * c2;                                   // pi g
+    constexpr float C = 0.923879532511286756f, S = 0.382683432365089772f;   // cos, sin of pi / 8
+    cw = flip ? fmaf(C, c8, S * s8) : c8;
+    sw = flip ? fmaf(S, c8, -C * s8) : s8;
+}
+
+// The 16 taps at source position k0 + frac, rows read through row(t) for
+// t = -7 ... 8.  Weight h_t = sinc(x) w(x), x = frac - t,
+// w(x) = 0.5 (1 + cos(2 pi x / 16)).  With sin(pi x) = (-1)^t sin(pi frac) and
+// cos(2 pi x / 16) = cw cos_t + sw sin_t = u_t, cos_t, sin_t the cos and sin of
+// 2 pi t / 16:
+//   h_t = (sin(pi frac) / (2 pi)) (-1)^t (1 + u_t) / x.
+// Taps t and t + 8 share (-1)^t and have u_{t+8} = -u_t.
+template <class Row>
+__device__ __forceinline__ float2 rc_interp(float frac, Row row) {
+    if (frac == 0.f) return row(0);   // h_0 = 1, every other tap sits on a zero of the sinc
+    float cw, sw, s;
+    rc_trig(frac, cw, sw, s);
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int t = -TAPS / 2 + 1; t <= TAPS / 2; ++t) {
-        const int k = k0 + t;
-        if (k < 0 || k >= n_range) continue;
-        const float x = frac - (float)t;
-        // sin(pi (frac - t)) = (-1)^t sin(pi frac); window 0.5 (1 + cos(2 pi x / TAPS))
-        const float sgn = (t & 1) ? -1.f : 1.f;
-        const float sinc = (x == 0.f) ? 1.f : sgn * s0 / (3.14159265358979f * x);
-        static_assert(TAPS == 16, "the window table holds 16 taps");
+    for (int t = -7; t <= 0; ++t) {
         const float2 cs = kHann16[t + 7];
-        // cos(2 pi (frac - t) / 16) = cos(2 pi frac/16) cos(2 pi t/16) + sin(2 pi frac/16) sin(2 pi t/16)
-        const float win = 0.5f + 0.5f * (cw * cs.x + sw * cs.y);
-        const float h = (fabsf(x) < 0.5f * TAPS) ? sinc * win : 0.f;
-        const float2 v = in[(int64_t)k * n_f + j];
-        acc.x = fmaf(h, v.x, acc.x);
-        acc.y = fmaf(h, v.y, acc.y);
+        const float u = fmaf(cw, cs.x, sw * cs.y);
+        const float r1 = rc_rcp(frac - (float)t), r2 = rc_rcp(frac - (float)(t + 8));
+        float h1 = fmaf(u, r1, r1), h2 = fmaf(-u, r2, r2);
+        if (t & 1) {
+            h1 = -h1;
+            h2 = -h2;
+        }
+        const float2 v1 = row(t), v2 = row(t + 8);
+        acc.x = fmaf(h1, v1.x, acc.x);
+        acc.y = fmaf(h1, v1.y, acc.y);
+        acc.x = fmaf(h2, v2.x, acc.x);
+        acc.y = fmaf(h2, v2.y, acc.y);
     }
-    out[idx] = acc;
+    const float a = s * 0.159154943091895336f;   // sin(pi frac) / (2 pi)
+    return make_float2(acc.x * a, acc.y * a);
+}
+
+__global__ void __launch_bounds__(kRcCols * kRcWarps)
+rcmc_tile_kernel(const float2* __restrict__ in, float2* __restrict__ out, int n_range, int n_f,
+                 const RdColumn* __restrict__ cols, float rn_hi, float rn_lo, int staged_rows) {
+    extern __shared__ float2 tile[];   // [staged_rows][32]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int j = blockIdx.x * kRcCols + lane;
+    const int n0 = blockIdx.y * kRcRows;
+    const int n1 = min(n0 + kRcRows, n_range) - 1;
+    const bool jok = j < n_f;
+    const RdColumn c = cols[jok ? j : n_f - 1];
+    // the rows this block reads: the same positions every output computes, so
+    // every warp finds the same span
+    int k_first, k_last;
+    float f_unused;
+    rc_locate(n0, c, rn_hi, rn_lo, k_first, f_unused);
+    rc_locate(n1, c, rn_hi, rn_lo, k_last, f_unused);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        k_first = min(k_first, __shfl_xor_sync(0xffffffffu, k_first, o));
+        k_last = max(k_last, __shfl_xor_sync(0xffffffffu, k_last, o));
+    }
+    const int lo = k_first - 7, hi = k_last + 8;
+    const int span = hi - lo + 1;
+    const bool staged = span <= staged_rows;
+    if (staged) {
+#pragma unroll 4
+        for (int rr = warp; rr < span; rr += kRcWarps) {
+            const int k = lo + rr;
+            tile[rr * kRcCols + lane] =
+                (jok && k >= 0 && k < n_range) ? in[(int64_t)k * n_f + j] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+    }
+    if (!jok) return;
+    for (int n = n0 + warp; n <= n1; n += kRcWarps) {
+        int k0;
+        float frac;
+        rc_locate(n, c, rn_hi, rn_lo, k0, frac);
+        float2 y;
+        if (staged) {
+            k0 = min(max(k0, lo + 7), hi - 8);   // already within; keeps every read inside the tile
+            const float2* b = tile + (k0 - lo) * kRcCols + lane;
+            y = rc_interp(frac, [&](int t) { return b[t * kRcCols]; });
+        } else {
+            y = rc_interp(frac, [&](int t) {
+                const int k = k0 + t;
+                return (k >= 0 && k < n_range) ? in[(int64_t)k * n_f + j] : make_float2(0.f, 0.f);
+            });
+        }
+        __stcs(out + (int64_t)n * n_f + j, y);
+    }
 }
 
 // Azimuth compression of range bin `line` (r = r_near + line): multiply the
@@ -106,7 +204,7 @@ az_compress_rd_kernel(const float2* in, float2* out, int64_t n_lines, const floa
         for (int r = 0; r < SC::R1; ++r) {
             const int j = lo + r * SC::S1;
             const RdColumn c = cols[j];
-            const float p = r_hi * c.a_hi;
+            const float p = __fmul_rn(r_hi, c.a_hi);          // never contracted into p - rint(p)
             const float e = fmaf(r_hi, c.a_hi, -p);           // exact error of the product
             const float frac = (p - rintf(p)) + (e + fmaf(r_hi, c.a_lo, r_lo * c.a_hi));
             float sn, cs;
@@ -190,13 +288,43 @@ cudaError_t launch_az_compress_rd(int n, const float2* in, float2* out, int64_t 
 }
 
 cudaError_t launch_rcmc(int taps, const float2* in, float2* out, int n_range, int n_f, const void* cols,
-                        double r_near, cudaStream_t st) {
-    const int64_t total = (int64_t)n_range * n_f;
-    const unsigned blocks = (unsigned)((total + 255) / 256);
-    const RdColumn* c = (const RdColumn*)cols;
-    if (taps != 16) return cudaErrorInvalidValue;
-    rcmc_kernel<16><<<blocks, 256, 0, st>>>(in, out, n_range, n_f, c, r_near);
+                        double r_near, int staged_rows, cudaStream_t st) {
+    if (taps != 16 || n_range <= 0 || n_f <= 0) return cudaErrorInvalidValue;
+    if (staged_rows > kRcMaxStaged) staged_rows = 0;   // too wide: every block reads global memory
+    const size_t smem = (size_t)staged_rows * kRcCols * sizeof(float2);
+    if (smem > 48 * 1024) {
+        cudaError_t e =
+            cudaFuncSetAttribute(rcmc_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const float rn_hi = (float)r_near, rn_lo = (float)(r_near - (double)rn_hi);
+    const dim3 grid((unsigned)((n_f + kRcCols - 1) / kRcCols), (unsigned)((n_range + kRcRows - 1) / kRcRows));
+    rcmc_tile_kernel<<<grid, kRcCols * kRcWarps, smem, st>>>(in, out, n_range, n_f, (const RdColumn*)cols, rn_hi,
+                                                            rn_lo, staged_rows);
     return cudaGetLastError();
+}
+
+// Host: rows a tile must stage, the largest over every tile of the scene:
+// 128 bins + 15 taps + the spread of the shift r (1/D - 1) over the tile's
+// 32 columns and 128 bins, plus 4 rows of margin for rounding.
+int rcmc_staged_rows(int n_range, int n_f, double r_near, const void* host_cols) {
+    const RdColumn* c = (const RdColumn*)host_cols;
+    double spread = 0;
+    for (int g = 0; g < n_f; g += kRcCols) {
+        double mn = 1e300, mx = -1e300;
+        for (int j = g; j < g + kRcCols && j < n_f; ++j) {
+            const double m = (double)c[j].mig_hi + (double)c[j].mig_lo;
+            mn = m < mn ? m : mn;
+            mx = m > mx ? m : mx;
+        }
+        for (int n0 = 0; n0 < n_range; n0 += kRcRows) {
+            const int n1 = (n0 + kRcRows < n_range ? n0 + kRcRows : n_range) - 1;
+            const double d = (r_near + n1) * mx - (r_near + n0) * mn;
+            spread = d > spread ? d : spread;
+        }
+    }
+    const double rows = kRcRows + 15 + ceil(spread) + 4;
+    return rows > kRcMaxStaged ? kRcMaxStaged + 1 : (int)rows;
 }
 
 // Host: the per-frequency columns of a geometry, FP64 then rounded.

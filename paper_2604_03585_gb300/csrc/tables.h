@@ -23,7 +23,8 @@ const char *rd_az_schedule(int n);
 cudaError_t launch_az_compress_rd(int n, const float2 *in, float2 *out, int64_t n_lines, const float2 *tw,
                                   const void *cols, double r_near, cudaStream_t st);
 cudaError_t launch_rcmc(int taps, const float2 *in, float2 *out, int n_range, int n_f, const void *cols,
-                        double r_near, cudaStream_t st);
+                        double r_near, int staged_rows, cudaStream_t st);
+int rcmc_staged_rows(int n_range, int n_f, double r_near, const void *host_cols);
 void rd_columns(int n_f, double kappa, double vs, void *host_cols);
 size_t rd_column_bytes();
 int corner_turn_variant();

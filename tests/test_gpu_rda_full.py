@@ -69,6 +69,36 @@ def test_full_rda_4096_vs_oracle(sar):
         assert M.peak(img, (n0, a0)) == M.peak(ref, (n0, a0)) == (n0, a0)
 
 
+@pytest.mark.parametrize("n_range,n_az,geo", [
+    (512, 256, sarsim.Geometry(10.0, 0.3, 4000.0)),
+    (1024, 4096, sarsim.Geometry(10.0, 0.3, 4000.0)),   # bins up to 5000: FP32 spacing 5e-4
+    (4096, 512, sarsim.Geometry(2.0, 0.3, 100.0)),      # D down to 0.55: shifts up to ~3400 bins
+    (256, 1024, sarsim.Geometry(5.0, 0.11, 37.3)),      # fractional r_near, kappa v_s = 0.55
+])
+def test_rcmc_vs_oracle(sar, n_range, n_az, geo):
+    """RCMC alone on white complex Gaussian range-Doppler data: every
+    interpolation weight shows in the output, element by element."""
+    orc = oracle.default()
+    rd = sarsim.complex_gaussian(17, 0, n_range * n_az, 1.0).reshape(n_range, n_az)
+    ref = orc.rcmc(rd, geo, taps=16)
+    x = torch.from_numpy(rd).cuda()
+    y = torch.empty_like(x)
+    dummy = torch.zeros(max(n_range, n_az), dtype=torch.complex64, device="cuda")
+    plan = sar.sar_plan_create(n_range, n_az, dummy[:n_range], dummy[:n_az])
+    sar.sar_plan_set_geometry(plan, *geo.as_tuple(), 16)
+    sar.sar_rcmc(plan, x, y)
+    torch.cuda.synchronize()
+    got = y.cpu().numpy()
+    plan.destroy()
+    # FP32 weights on unit-variance data: ~16 taps x 1e-7 relative each
+    err = np.abs(got - ref)
+    scale = np.sqrt(np.mean(np.abs(ref) ** 2))
+    print(f"\nRCMC {n_range}x{n_az} kappa={geo.kappa} v_s={geo.v_s}: max {err.max() / scale:.2e} "
+          f"rel_l2 {M.rel_l2(got, ref):.2e}")
+    assert M.rel_l2(got, ref) < 2e-6
+    assert err.max() < 2e-5 * scale
+
+
 def test_geometry_refusals(sar):
     x = torch.zeros(256, dtype=torch.complex64, device="cuda")
     plan = sar.sar_plan_create(256, 256, x, x)
@@ -79,4 +109,11 @@ def test_geometry_refusals(sar):
     y = torch.empty((256, 256), dtype=torch.complex64, device="cuda")
     with pytest.raises(sar.SarError):
         sar.sar_rda_full(plan, y, torch.empty_like(y), torch.empty_like(y))   # no geometry yet
+    with pytest.raises(sar.SarError):
+        sar.sar_rcmc(plan, y, torch.empty_like(y))                           # no geometry yet
+    sar.sar_plan_set_geometry(plan, 10.0, 0.3, 100.0, 0)
+    with pytest.raises(sar.SarError):
+        sar.sar_rcmc(plan, y, torch.empty_like(y))                           # taps = 0
+    with pytest.raises(sar.SarError):
+        sar.sar_rcmc(plan, y, y)                                             # overlap
     plan.destroy()
