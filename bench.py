@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--azimuth-schedule", default=None, help="schedule of the azimuth pass (default: autotuned)")
     ap.add_argument("--no-autotune", action="store_true", help="use the compiled-in preferred schedules")
     ap.add_argument("--no-extras", action="store_true", help="skip the ragged-batch and serving measurements")
+    ap.add_argument("--extras", default="unfused,precision,rda_full,ragged_batch,serving",
+                    help="comma-separated extra measurements to run after the headline step")
     return ap.parse_args()
 
 
@@ -564,11 +566,19 @@ def main():
                          f"{nth} threads), scaled x{N_AZ // lines} to one scene"}
 
     extras = {}
-    if not args.no_extras:
+    wanted = set() if args.no_extras else {x.strip() for x in args.extras.split(",") if x.strip()}
+    unknown = wanted - {"unfused", "precision", "rda_full", "ragged_batch", "serving"}
+    if unknown:
+        raise SystemExit(f"bench.py: unknown extras {sorted(unknown)}")
+    if "unfused" in wanted:
         extras["unfused"] = unfused_bench(sar, plan, raws[0], work, image, stream, ms_step)
+    if "precision" in wanted:
         extras["precision"] = precision_bench(sar, Hr, Ha, raws[0], work, image, stream)
+    if "rda_full" in wanted:
         extras["rda_full"] = rda_full_bench(sar, dev, stream, work, image)
+    if "ragged_batch" in wanted:
         extras["ragged_batch"] = ragged_batch_bench(sar, roofline, dev, stream, peak)
+    if "serving" in wanted:
         extras["serving"] = serving_bench(sar, dev, stream)
 
     value = job_value(ms_step, world)

@@ -257,15 +257,19 @@ __device__ __forceinline__ void fused_range_ct_body(const float2* in, float2* im
 }
 
 // The same fold with one line per block and QC blocks per thread-block
-// cluster (QC = 4, 8 or 16): each block compresses its own line and parks it,
-// in natural order, in its shared memory; after a cluster barrier block k of
-// the cluster gathers range bins [k N/QC, (k+1) N/QC) of all QC lines through
-// distributed shared memory and writes each bin's QC samples as one
-// QC*8-byte chunk of image row n (with QC = 16 a full 128-byte line, written
-// by eight lanes of 16 bytes).  A block needs one line of shared memory, not
-// QC, so an SM keeps as many lines in flight as the unfolded kernel.  A second
-// cluster barrier keeps every block's shared memory alive until its
-// neighbours have read it.  Launched with a cluster dimension of QC.
+// cluster (QC = 4, 8 or 16).  Block q of the cluster compresses line a0 + q;
+// block k owns range bins [k N/QC, (k+1) N/QC) of the image rows.  After a
+// cluster barrier (every block is done with its shared memory for the FFT)
+// each block pushes its line, straight from the registers of the last pass,
+// into the owners' shared memory, line-major (recv[q][j], bin j of line q), so
+// that a warp's 32 remote stores form one contiguous 256-byte run.  Remote
+// stores do not stall the issuing warp.  After a second barrier (every push
+// has landed) each block reads its own shared memory and writes each bin's QC
+// samples as one QC*8-byte chunk of image row n, image[n][a0 .. a0+QC-1] (two
+// lines, 16 bytes, per lane); no block touches another's shared memory after
+// that barrier.  A block needs one line of shared memory, not QC, so an SM
+// keeps as many lines in flight as the unfolded kernel.  Launched with a
+// cluster dimension of QC.
 template <class SC, int QC, bool ROLL>
 __device__ __forceinline__ void fused_range_ct_cluster_body(const float2* in, float2* img, int64_t ld_in,
                                                             int64_t ld_img, const float2* filt,
@@ -291,24 +295,31 @@ __device__ __forceinline__ void fused_range_ct_cluster_body(const float2* in, fl
 #pragma unroll
         for (int r = 0; r < R1; ++r) v[s * R1 + r] = x[r];
     }
-    __syncthreads();
+    static_assert(QC == 4 || QC == 8 || QC == 16, "clusters of 4, 8 or 16 lines");
+    constexpr int NQ = SC::N / QC;   // range bins owned by one block
+    static_assert(SC::SMEM_ELEMS >= SC::N, "the receive buffer is one line");
+    cluster.sync();
+    // push: natural-order sample i = lo + r S1 of line a0 + rank goes to
+    // block i / NQ, slot rank NQ + i mod NQ
 #pragma unroll
     for (int s = 0; s < G1; ++s) {
         const int lo = t + SC::T * s;
 #pragma unroll
-        for (int r = 0; r < R1; ++r) sm[lo + r * S1] = v[s * R1 + r];
+        for (int r = 0; r < R1; ++r) {
+            const int i = lo + r * S1;
+            float2* dst = cluster.map_shared_rank(sm, i / NQ);
+            dst[rank * NQ + i % NQ] = v[s * R1 + r];
+        }
     }
     cluster.sync();
-    constexpr int NQ = SC::N / QC;       // range bins gathered by this block
-    constexpr int LPN = QC / 2;          // lanes per bin, 16 bytes (two lines) each
+    constexpr int LPN = QC / 2;   // lanes per bin, 16 bytes (two lines) each
+#pragma unroll 4
     for (int idx = t; idx < NQ * LPN; idx += SC::T) {
-        const int n = rank * NQ + idx / LPN;
-        const int p = idx % LPN;
-        const float2 c0 = cluster.map_shared_rank(sm, 2 * p)[n];
-        const float2 c1 = cluster.map_shared_rank(sm, 2 * p + 1)[n];
-        __stcs(reinterpret_cast<float4*>(img + (int64_t)n * ld_img + a0 + 2 * p), make_float4(c0.x, c0.y, c1.x, c1.y));
+        const int j = idx / LPN, p = idx % LPN;
+        const float2 c0 = sm[(2 * p) * NQ + j], c1 = sm[(2 * p + 1) * NQ + j];
+        __stcs(reinterpret_cast<float4*>(img + (int64_t)(rank * NQ + j) * ld_img + a0 + 2 * p),
+               make_float4(c0.x, c0.y, c1.x, c1.y));
     }
-    cluster.sync();
 }
 
 template <class SC, int QC, bool ROLL>
