@@ -28,7 +28,14 @@
  *     device surfaces on a later call or on sar_sync().  sar_last_error()
  *     gives a message for the calling thread's last failure.
  *   - No C++ exception crosses this interface.
- *   - Supported line lengths: powers of two from 256 to 16384.
+ *   - Supported line lengths: powers of two from 256 to 131072.  Lines up to
+ *     16384 samples run one line per thread block; longer lines run one line
+ *     per thread-block cluster of 2 to 16 blocks exchanging it through
+ *     distributed shared memory (sar_range_compress, sar_azimuth_compress,
+ *     sar_rda_process[_oop|_host|_unfused], sar_fft_lines,
+ *     sar_make_lfm_spectrum, sar_autotune).  The folded corner turn, split
+ *     precision, ragged batches, the full processor's azimuth length and
+ *     sar_fft_lines_static stop at 16384 (SAR_ERR_UNSUPPORTED above).
  */
 #ifndef SAR_GB300_H
 #define SAR_GB300_H
@@ -54,7 +61,7 @@ typedef struct sar_plan_s *sar_plan; /* opaque; immutable after creation; usable
 typedef enum {
     SAR_OK = 0,
     SAR_ERR_INVALID_ARG = 1,   /* null/misaligned pointer, size out of range, bad flag */
-    SAR_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement (e.g. N > 16384) */
+    SAR_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement (e.g. N > 131072) */
     SAR_ERR_OUT_OF_MEMORY = 3, /* a plan allocation failed; nothing was leaked */
     SAR_ERR_CUDA = 4,          /* a CUDA runtime call or launch failed */
     SAR_ERR_TIMEOUT = 5        /* a bounded device-side wait gave up */
@@ -92,7 +99,8 @@ typedef struct {
 #define SAR_PLAN_UNFOLDED_CORNER_TURN 1u
 
 /* Create a plan for an n_az x n_range scene (Sec. IV-A, the N_a x N_r data
- * matrix).  n_range and n_az: powers of two in [256, 16384].  Allocates the
+ * matrix).  n_range and n_az: powers of two in [256, 131072] (above 16384 on
+ * thread-block clusters, without the folded corner turn).  Allocates the
  * plan's device tables on the current device, builds them (FP64 twiddle
  * phases rounded to FP32) and synchronises the device once; not for the hot
  * loop.  *out receives the plan, or NULL on failure. */
@@ -203,7 +211,7 @@ SAR_API sar_status sar_rda_process_host(sar_plan plan, const void *raw, void *im
  * product tbp, c(m) = exp(i pi (tbp/n_chirp^2) m^2), m = -n_chirp/2 ...
  * n_chirp/2 - 1, centred on index 0 of the length-n line (wrapping).  The
  * chirp phase is evaluated in FP64 on the device and rounded to FP32; the
- * transform is this library's FP32 FFT.  n: power of two in [256, 16384];
+ * transform is this library's FP32 FFT.  n: power of two in [256, 131072];
  * 1 <= n_chirp <= n; tbp > 0. */
 SAR_API sar_status sar_make_lfm_spectrum(int64_t n, int64_t n_chirp, double tbp, void *out, sar_stream stream);
 
@@ -225,7 +233,7 @@ SAR_API sar_status sar_simulate_echo(int64_t n_az, int64_t n_range, const int64_
 /* Unnormalised DFT of n_lines lines of length n (natural order in and out):
  * out[l][k] = sum_j in[l][j] exp(-+2 pi i j k / n), '+' when inverse != 0
  * (computed as conj(FFT(conj x)), Sec. II-C).  in and out: device
- * complex64[n_lines][n]; in place allowed.  n: power of two in [256, 16384].
+ * complex64[n_lines][n]; in place allowed.  n: power of two in [256, 131072].
  * Exposes the line FFT engine on its own (tests, filter design). */
 SAR_API sar_status sar_fft_lines(int64_t n, int64_t n_lines, const void *in, void *out, int inverse, sar_stream stream);
 
@@ -313,8 +321,8 @@ SAR_API sar_status sar_batch_destroy(sar_batch batch);
 typedef struct {
     int32_t n_classes;                   /* size classes */
     int32_t max_inflight;                /* concurrent requests, 1 ... 256 */
-    const int64_t *n_range;              /* [n_classes] powers of two in [256, 16384] */
-    const int64_t *n_az;                 /* [n_classes] powers of two in [256, 16384] */
+    const int64_t *n_range;              /* [n_classes] powers of two in [256, 131072] */
+    const int64_t *n_az;                 /* [n_classes] powers of two in [256, 131072] */
     const void *const *pool;             /* [n_classes] device complex64[n_az][n_range] echoes to ingest */
     const void *const *range_spectrum;   /* [n_classes] device complex64[n_range] */
     const void *const *az_spectrum;      /* [n_classes] device complex64[n_az] */
@@ -361,10 +369,14 @@ SAR_API sar_status sar_server_destroy(sar_server server);
  * shared memory.  Several schedules are compiled per N; which one is fastest
  * depends on the GPU, so a plan takes the process-wide preferred schedule of
  * each length (the first compiled one until sar_autotune or
- * sar_set_preferred_schedule changes it), or names one explicitly. */
+ * sar_set_preferred_schedule changes it), or names one explicitly.
+ * cluster_blocks > 1: one line per cluster of that many blocks; e, r1..r3,
+ * threads_per_block and smem_bytes then describe each block's
+ * n / cluster_blocks point part of the line. */
 typedef struct {
     char name[48];
     int32_t n, e, r1, r2, r3, lines_per_block, threads_per_block, smem_bytes;
+    int32_t cluster_blocks;
 } sar_schedule_desc;
 
 /* Number of compiled schedules, and the description of schedule `index`

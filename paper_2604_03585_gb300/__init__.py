@@ -50,7 +50,7 @@ class sar_schedule_desc(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("n", ctypes.c_int32), ("e", ctypes.c_int32),
                 ("r1", ctypes.c_int32), ("r2", ctypes.c_int32), ("r3", ctypes.c_int32),
                 ("lines_per_block", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
-                ("smem_bytes", ctypes.c_int32)]
+                ("smem_bytes", ctypes.c_int32), ("cluster_blocks", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: (getattr(self, f).decode() if f == "name" else getattr(self, f)) for f, _ in self._fields_}

@@ -135,6 +135,8 @@ sar_status sar_batch_create(const sar_strip *strips, int32_t count, uint32_t fla
     for (int32_t i = 0; i < count; ++i) {
         const sar_strip &s = strips[i];
         if ((st = sar::validate_length(s.n_range, "strip n_range")) != SAR_OK) return st;
+        if (s.n_range > 16384)
+            return sar::report_error(SAR_ERR_UNSUPPORTED, "strip n_range must be at most 16384");
         if (s.n_az < 1 || s.n_az > 16384)
             return sar::report_error(SAR_ERR_UNSUPPORTED, "strip n_az must be in [1, 16384]");
         if ((st = sar::validate_device_ptr(s.raw, "strip raw")) != SAR_OK) return st;

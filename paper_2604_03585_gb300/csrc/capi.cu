@@ -45,8 +45,8 @@ bool is_pow2(int64_t n) { return n >= 1 && (n & (n - 1)) == 0; }
 
 sar_status check_length(int64_t n, const char *what) {
     if (n < 1) return fail(SAR_ERR_INVALID_ARG, "%s = %lld must be >= 1", what, (long long)n);
-    if (!is_pow2(n) || n < 256 || n > 16384)
-        return fail(SAR_ERR_UNSUPPORTED, "%s = %lld: supported lengths are powers of two in [256, 16384]", what,
+    if (!is_pow2(n) || n < 256 || n > 131072)
+        return fail(SAR_ERR_UNSUPPORTED, "%s = %lld: supported lengths are powers of two in [256, 131072]", what,
                     (long long)n);
     return SAR_OK;
 }
@@ -315,6 +315,7 @@ static void describe(const SchedDesc &d, sar_schedule_desc *o) {
     o->lines_per_block = d.lpb;
     o->threads_per_block = d.threads;
     o->smem_bytes = d.smem_bytes;
+    o->cluster_blocks = d.cluster > 1 ? d.cluster : 1;
 }
 
 int32_t sar_schedule_count(void) { return sar::schedule_count(); }
@@ -674,15 +675,16 @@ sar_status sar_rda_full(sar_plan p, const void *raw, void *work, void *image, sa
     if (overlaps(raw, work, bytes) || overlaps(raw, image, bytes) || overlaps(work, image, bytes))
         return fail(SAR_ERR_INVALID_ARG, "raw, work and image must not overlap");
     cudaStream_t s = (cudaStream_t)stream;
-    // 1. range compression and corner turn: raw -> image [n_range][n_az]
-    if ((st = sar_rda_process_oop_range(p, raw, work, image, s)) != SAR_OK) return st;
-    // 2. azimuth FFT of every range bin, in place
+    const char *az_name = sar::rd_az_schedule((int)p->n_az);
+    const SchedDesc *dz = az_name ? sar::find_schedule(az_name) : nullptr;
+    if (!dz) return fail(SAR_ERR_UNSUPPORTED, "full processing needs n_az <= 16384");
     const SchedDesc &da = *p->az.sched;
     float2 *tw_fft = nullptr, *tw_az = nullptr;
     if ((st = cached_twiddles(&da, &tw_fft)) != SAR_OK) return st;
-    const SchedDesc *dz = sar::find_schedule(sar::rd_az_schedule((int)p->n_az));
-    if (!dz) return fail(SAR_ERR_UNSUPPORTED, "no azimuth schedule for this length");
     if ((st = cached_twiddles(dz, &tw_az)) != SAR_OK) return st;
+    // 1. range compression and corner turn: raw -> image [n_range][n_az]
+    if ((st = sar_rda_process_oop_range(p, raw, work, image, s)) != SAR_OK) return st;
+    // 2. azimuth FFT of every range bin, in place
     cudaError_t e = da.dft((const float2 *)image, (float2 *)image, p->n_range, p->n_az, (int)p->n_az, tw_fft, 0, s);
     if (e != cudaSuccess) return cuda_fail(e, "azimuth FFT launch");
     // 3. RCMC image -> work (or no correction: work <- image)

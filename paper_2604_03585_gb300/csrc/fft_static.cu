@@ -81,6 +81,11 @@ extern "C" sar_status sar_fft_lines_static(int64_t n, int64_t n_lines, const voi
                                            sar_stream stream) {
     sar_status st;
     if ((st = sar::validate_length(n, "n")) != SAR_OK) return st;
+    const sar::SchedDesc *d = sar::default_schedule((int)n);
+    if (!d) return sar::report_error(SAR_ERR_UNSUPPORTED, "no compiled schedule for this length");
+    if (d->tw_elems > kStaticTwiddleElems)
+        return sar::report_error(SAR_ERR_UNSUPPORTED,
+                                 "this length needs a twiddle table larger than the static 32768-entry array");
     if (n_lines < 0) return sar::report_error(SAR_ERR_INVALID_ARG, "n_lines < 0");
     if (n_lines == 0) return SAR_OK;
     if ((st = sar::validate_device_ptr(in, "in")) != SAR_OK) return st;
@@ -89,11 +94,6 @@ extern "C" sar_status sar_fft_lines_static(int64_t n, int64_t n_lines, const voi
     const char *a = (const char *)in, *b = (const char *)out;
     if (a != b && a < b + bytes && b < a + bytes)
         return sar::report_error(SAR_ERR_INVALID_ARG, "in and out partially overlap");
-    const sar::SchedDesc *d = sar::default_schedule((int)n);
-    if (!d) return sar::report_error(SAR_ERR_UNSUPPORTED, "no compiled schedule for this length");
-    if (d->tw_elems > kStaticTwiddleElems)
-        return sar::report_error(SAR_ERR_UNSUPPORTED,
-                                 "this length needs a twiddle table larger than the static 32768-entry array");
     float2 *tw = nullptr;
     if ((st = static_twiddles(*d, &tw)) != SAR_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;

@@ -9,14 +9,14 @@ namespace sar {
 
 namespace {
 struct All {
-    const SchedDesc *p[64];
+    const SchedDesc *p[96];
     int n = 0;
     All() {
-        const SchedDesc *(*tables[])(int *) = {schedules_small, schedules_4096, schedules_large};
+        const SchedDesc *(*tables[])(int *) = {schedules_small, schedules_4096, schedules_large, schedules_cluster};
         for (auto f : tables) {
             int c = 0;
             const SchedDesc *t = f(&c);
-            for (int i = 0; i < c && n < 64; ++i) p[n++] = &t[i];
+            for (int i = 0; i < c && n < 96; ++i) p[n++] = &t[i];
         }
     }
 };
@@ -87,7 +87,8 @@ void set_preferred_ct_schedule(const SchedDesc *d) {
 }
 
 void filter_slot_to_k(const SchedDesc &d, int32_t *idx) {
-    const int N = d.n, E = d.e, T = N / E, RL = d.rl;
+    const int C = d.cluster > 1 ? d.cluster : 1;
+    const int N = d.n / C, E = d.e, T = N / E, RL = d.rl;   // N: the per-block engine's length
     const int S1 = N / d.r1;
     const int S2 = S1 / d.r2;
     for (int t = 0; t < T; ++t)
@@ -100,7 +101,7 @@ void filter_slot_to_k(const SchedDesc &d, int32_t *idx) {
                 k = k1 + d.r1 * ((rem / S2) + d.r2 * (rem % S2));
             else
                 k = k1 + d.r1 * rem;
-            idx[j * T + t] = k;
+            for (int c = 0; c < C; ++c) idx[c * N + j * T + t] = c + C * k;
         }
 }
 

@@ -46,12 +46,17 @@ struct SchedDesc {
     fused_ct_fn fused_ct;   // nullptr: no folded corner turn for this schedule
     int ct_lines;           // lines per block of fused_ct (n_lines must be a multiple)
     seg_fn fused_seg;       // nullptr: no segment-table kernel for this schedule
+    int cluster;            // > 1: one line per cluster of this many blocks, N = cluster * (n / cluster);
+                            // e, r1..r3, rl, threads and smem_bytes then describe each block's
+                            // M = n / cluster point engine, and the twiddle table is the M-point
+                            // engine's followed by W_N^j for j < n
 };
 
 // All compiled schedules (one table per translation unit).
 const SchedDesc *schedules_small(int *count);   // N = 256 .. 2048
 const SchedDesc *schedules_4096(int *count);
 const SchedDesc *schedules_large(int *count);   // N = 8192, 16384
+const SchedDesc *schedules_cluster(int *count); // N = 32768 ... 131072, one line per cluster
 
 // The preferred schedule for length n, or nullptr.
 const SchedDesc *default_schedule(int n);
@@ -66,7 +71,9 @@ const SchedDesc *schedule_at(int i);
 
 // Host-side permutation of the matched filter into the fused kernel's
 // register order: slot j*T + t  (j = s*RL + r)  holds natural frequency
-// index k of position P = (t + T*s)*RL + r.
+// index k of position P = (t + T*s)*RL + r.  For a cluster schedule, block
+// k1's slice (slots k1*M ... k1*M + M - 1) holds k = k1 + C*k_M with k_M the
+// M-point engine's index of that slot.
 void filter_slot_to_k(const SchedDesc &d, int32_t *idx /* n entries */);
 
 }  // namespace sar

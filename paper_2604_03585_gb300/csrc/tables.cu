@@ -17,6 +17,15 @@ __global__ void twiddle_table_kernel(float2 *tw, int R, int S, int M) {
     tw[i] = make_float2((float)c, (float)s);
 }
 
+// out[j] = exp(-2 pi i j / n), j < n, evaluated like the twiddles above.
+__global__ void roots_table_kernel(float2 *out, int n) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double s, c;
+    sincospi(-2.0 * (double)j / (double)n, &s, &c);
+    out[j] = make_float2((float)c, (float)s);
+}
+
 // One length-n line holding the chirp c(m) = exp(i pi K m^2), K = tbp/nc^2,
 // m = -nc/2 ... nc/2 - 1, at position m mod n; zero elsewhere.  The phase in
 // units of pi, tbp*m^2/nc^2, is reduced modulo 2 in FP64 before sincospi().
@@ -81,14 +90,17 @@ cudaError_t build_natural_filter(const float2 *H, float2 *dst, int n, cudaStream
 }
 
 cudaError_t build_twiddles(const SchedDesc &d, float2 *tw, cudaStream_t st) {
-    const int S1 = d.n / d.r1;
+    const int M = d.cluster > 1 ? d.n / d.cluster : d.n;   // the per-block engine's length
+    const int S1 = M / d.r1;
     int total = d.r1 * S1;
-    twiddle_table_kernel<<<(total + 255) / 256, 256, 0, st>>>(tw, d.r1, S1, d.n);
+    twiddle_table_kernel<<<(total + 255) / 256, 256, 0, st>>>(tw, d.r1, S1, M);
     if (d.r3 > 1) {
         const int S2 = S1 / d.r2;
         const int t2 = d.r2 * S2;
         twiddle_table_kernel<<<(t2 + 255) / 256, 256, 0, st>>>(tw + total, d.r2, S2, S1);
+        total += t2;
     }
+    if (d.cluster > 1) roots_table_kernel<<<(d.n + 255) / 256, 256, 0, st>>>(tw + total, d.n);
     return cudaGetLastError();
 }
 

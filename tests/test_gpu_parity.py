@@ -469,7 +469,7 @@ def test_bad_arguments_are_refused(sar):
         sar.sar_plan_create(256, 256 * 3, Hr, Ha)
     assert e.value.status == sar.SAR_ERR_UNSUPPORTED
     with pytest.raises(sar.SarError) as e:
-        sar.sar_plan_create(256, 32768, Hr, Ha)
+        sar.sar_plan_create(256, 262144, Hr, Ha)
     assert e.value.status == sar.SAR_ERR_UNSUPPORTED
     sar.sar_rda_process(plan, good, other)                   # still usable afterwards
     sar.sar_sync()
