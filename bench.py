@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--azimuth-schedule", default=None, help="schedule of the azimuth pass (default: autotuned)")
     ap.add_argument("--no-autotune", action="store_true", help="use the compiled-in preferred schedules")
     ap.add_argument("--no-extras", action="store_true", help="skip the ragged-batch and serving measurements")
-    ap.add_argument("--extras", default="unfused,precision,rda_full,ragged_batch,serving",
+    ap.add_argument("--extras", default="unfused,precision,rda_full,long_lines,ragged_batch,serving",
                     help="comma-separated extra measurements to run after the headline step")
     return ap.parse_args()
 
@@ -284,6 +284,25 @@ def precision_bench(sar, Hr, Ha, raw, work, image, stream, reps: int = 50) -> di
         plan.destroy()
     out["note"] = ("unfolded three-kernel path for every precision; error against the FP64 oracle: "
                    "profiles/precision_4096.md")
+    return out
+
+
+# ---------------------------------------------------------------------------
+# lines longer than one block's shared memory (thread-block clusters)
+# ---------------------------------------------------------------------------
+
+def long_lines_bench(sar, stream, peak, reps: int = 10) -> dict:
+    """Fused pass (FFT, x H, IFFT per line) over 384 MiB of lines of 32768,
+    65536 and 131072 samples, every cluster schedule timed by the native
+    autotuner (median of `reps` launches); GB/s over 16 B per sample."""
+    out = {}
+    for n in (32768, 65536, 131072):
+        n_lines = (384 << 20) // (8 * n)
+        best, best_ms, all_ms = sar.sar_autotune(n, n_lines, reps=reps, stream=stream)
+        gbs = {k: 16.0 * n * n_lines / (ms * 1e-3) / 1e9 for k, ms in all_ms.items()}
+        out[str(n)] = {"lines": n_lines, "best": best["name"], "ms": best_ms,
+                       "gb_s": gbs[best["name"]], "frac_hbm": gbs[best["name"]] / peak,
+                       "all_gb_s": {k: round(v, 1) for k, v in sorted(gbs.items(), key=lambda x: -x[1])}}
     return out
 
 
@@ -567,7 +586,7 @@ def main():
 
     extras = {}
     wanted = set() if args.no_extras else {x.strip() for x in args.extras.split(",") if x.strip()}
-    unknown = wanted - {"unfused", "precision", "rda_full", "ragged_batch", "serving"}
+    unknown = wanted - {"unfused", "precision", "rda_full", "long_lines", "ragged_batch", "serving"}
     if unknown:
         raise SystemExit(f"bench.py: unknown extras {sorted(unknown)}")
     if "unfused" in wanted:
@@ -576,6 +595,8 @@ def main():
         extras["precision"] = precision_bench(sar, Hr, Ha, raws[0], work, image, stream)
     if "rda_full" in wanted:
         extras["rda_full"] = rda_full_bench(sar, dev, stream, work, image)
+    if "long_lines" in wanted:
+        extras["long_lines"] = long_lines_bench(sar, stream, peak)
     if "ragged_batch" in wanted:
         extras["ragged_batch"] = ragged_batch_bench(sar, roofline, dev, stream, peak)
     if "serving" in wanted:

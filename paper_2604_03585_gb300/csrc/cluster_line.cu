@@ -54,16 +54,17 @@ __device__ __forceinline__ void cluster_arrive_relaxed() {
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.aligned;" ::: "memory"); }
 
 // Step 1: C-point DFTs over n1 and the twiddle W_N^{n2 k1}, pushed to block
-// k1 at position n2, one n2 at a time (C values live).  roots[j] = W_N^j,
+// k1 at position n2 (PADDED: at the line engine's padded shared-memory slot of
+// n2), one n2 at a time (C values live).  roots[j] = W_N^j,
 // j < N.  The block announces itself on the cluster barrier at once and waits
 // for the others just before its first remote store.
-template <class SC, int C, bool RAGGED, bool CONJ_IN>
+template <class SC, int C, bool RAGGED, bool CONJ_IN, bool PADDED = false>
 __device__ __forceinline__ void cluster_first_stage(const float2* src, int valid, const float2* roots, int t,
                                                     int rank, float2* sm,
                                                     cooperative_groups::cluster_group& cluster) {
     using G = ClusterGeom<SC, C>;
     cluster_arrive_relaxed();
-#pragma unroll
+#pragma unroll(PADDED ? 2 : G::EQ)
     for (int i = 0; i < G::EQ; ++i) {
         const int n2 = rank * G::Q + t + SC::T * i;
         float2 a[C];
@@ -77,9 +78,9 @@ __device__ __forceinline__ void cluster_first_stage(const float2* src, int valid
         dft_reg<C, false>(a);
 #pragma unroll
         for (int k1 = 1; k1 < C; ++k1) a[k1] = cmul(a[k1], roots[n2 * k1]);
-        if (i == 0) cluster_wait();   // every block of the cluster is running
+        if (i == 0) cluster_wait();   // every block of the cluster is running (the first time round)
 #pragma unroll
-        for (int k1 = 0; k1 < C; ++k1) cluster.map_shared_rank(sm, k1)[n2] = a[k1];
+        for (int k1 = 0; k1 < C; ++k1) cluster.map_shared_rank(sm, k1)[PADDED ? smem_pos(n2, SC::PADSH) : n2] = a[k1];
     }
     cluster.sync();   // the pushes have landed
 }
@@ -150,6 +151,82 @@ cluster_fused_kernel(const float2* in, float2* out, int64_t ld, int valid, const
             if (!RAGGED || idx < valid) __stcs(dst + idx, b[n1]);
         }
     }
+}
+
+// The same compression with the M-point part group-streamed (streamed.cuh:
+// one radix group live in registers, rolled group loops), registers capped at
+// 128 per thread so that two 256-thread blocks fit on an SM.  Step 1 pushes into the receivers' padded
+// shared-memory slots, where the forward pass 1 runs in place like a middle
+// pass.  The inverse pass 1 writes its result, times W_N^{-n2 k1}, back in
+// place; after a cluster barrier each block pulls its own n2 range from every
+// block's shared memory (a receive buffer for a push would cost a second line
+// of shared memory), takes the inverse C-point DFTs and stores; a last
+// barrier keeps every block's shared memory until all pulls are done.
+template <class SC, int C, bool ROLL>
+__global__ void __launch_bounds__(SC::T, 65536 / (SC::T * 128) > 1 ? 65536 / (SC::T * 128) : 1)
+cluster_streamed_kernel(const float2* in, float2* out, int64_t ld, const float2* filt, const float2* tw) {
+    namespace cg = cooperative_groups;
+    using G = ClusterGeom<SC, C>;
+    extern __shared__ float2 smem_dyn[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int t = threadIdx.x;
+    const int rank = (int)cluster.block_rank();
+    const int64_t line = blockIdx.x / C;
+    float2* sm = smem_dyn;
+    const float2* roots = tw + SC::TW_ELEMS;
+    constexpr int R1 = SC::R1, S1 = SC::S1, G1 = SC::E / R1;
+    constexpr int RL = SC::RL, GL = SC::E / RL;
+    cluster_first_stage<SC, C, false, false, true>(in + line * ld, G::N, roots, t, rank, sm, cluster);
+    streamed_mid_pass<SC, R1, S1, false, ROLL>(sm, tw, t);
+    __syncthreads();
+    const float2* tw2 = tw + R1 * S1;
+    if constexpr (SC::P == 3) {
+        streamed_mid_pass<SC, SC::R2, SC::S2, false, ROLL>(sm, tw2, t);
+        __syncthreads();
+    }
+    // last forward pass, this block's filter slice, first inverse pass
+    const float2* fl = filt + (int64_t)rank * G::M;
+#pragma unroll(ROLL ? 1 : GL)
+    for (int s = 0; s < GL; ++s) {
+        const int g = t + SC::T * s;
+        float2 x[RL];
+        grp_smem_load<RL, 1>(sm, g * RL, SC::PADSH, x);
+        dft_reg<RL, false>(x);
+#pragma unroll
+        for (int r = 0; r < RL; ++r) x[r] = cmul(x[r], fl[(s * RL + r) * SC::T + t]);
+        dft_reg<RL, true>(x);
+        grp_smem_store<RL, 1>(sm, g * RL, SC::PADSH, x);
+    }
+    __syncthreads();
+    if constexpr (SC::P == 3) {
+        streamed_mid_pass<SC, SC::R2, SC::S2, true, ROLL>(sm, tw2, t);
+        __syncthreads();
+    }
+    // inverse pass 1 in place, natural n2 = lo + r S1, times W_N^{-n2 k1}
+#pragma unroll(ROLL ? 1 : G1)
+    for (int s = 0; s < G1; ++s) {
+        const int lo = t + SC::T * s;
+        float2 x[R1];
+        grp_smem_load<R1, S1>(sm, lo, SC::PADSH, x);
+        grp_twiddle<R1, S1, true>(tw, lo, x);
+        dft_reg<R1, true>(x);
+#pragma unroll
+        for (int r = 0; r < R1; ++r) x[r] = cmulc(x[r], roots[(lo + r * S1) * rank]);
+        grp_smem_store<R1, S1>(sm, lo, SC::PADSH, x);
+    }
+    cluster.sync();   // every block's inverse result is in place
+    float2* dst = out + line * ld;
+#pragma unroll 2
+    for (int i = 0; i < G::EQ; ++i) {
+        const int n2 = rank * G::Q + t + SC::T * i;
+        float2 b[C];
+#pragma unroll
+        for (int k1 = 0; k1 < C; ++k1) b[k1] = cluster.map_shared_rank(sm, k1)[smem_pos(n2, SC::PADSH)];
+        dft_reg<C, true>(b);
+#pragma unroll
+        for (int n1 = 0; n1 < C; ++n1) __stcs(dst + n1 * G::M + n2, b[n1]);
+    }
+    cluster.sync();   // keep this block's shared memory until every block has pulled
 }
 
 // Stand-alone FFT of a line, natural-order output (unnormalised; the inverse
@@ -244,6 +321,21 @@ cudaError_t launch_cluster_fused(const float2* in, float2* out, int64_t n_lines,
 }
 
 template <class SC, int C>
+cudaError_t prepare_cluster_streamed() {
+    cudaError_t e = cluster_attrs(cluster_streamed_kernel<SC, C, true>, cluster_smem<SC, C>(), C);
+    return e == cudaSuccess ? prepare_cluster<SC, C>() : e;
+}
+
+template <class SC, int C>
+cudaError_t launch_cluster_streamed(const float2* in, float2* out, int64_t n_lines, int64_t ld, int valid,
+                                    const float2* filt, const float2* tw, const FusedCtl&, cudaStream_t st) {
+    if (n_lines <= 0) return cudaSuccess;
+    if (valid != ClusterGeom<SC, C>::N) return cudaErrorInvalidValue;
+    return launch_on_clusters(cluster_streamed_kernel<SC, C, true>, n_lines, SC::T, cluster_smem<SC, C>(), C, st,
+                              in, out, ld, filt, tw);
+}
+
+template <class SC, int C>
 cudaError_t launch_cluster_dft(const float2* in, float2* out, int64_t n_lines, int64_t ld, int valid,
                                const float2* tw, int inverse, cudaStream_t st) {
     if (n_lines <= 0) return cudaSuccess;
@@ -254,7 +346,7 @@ cudaError_t launch_cluster_dft(const float2* in, float2* out, int64_t n_lines, i
     return launch_on_clusters(cluster_dft_kernel<SC, C, false>, n_lines, SC::T, smem, C, st, in, out, ld, valid, tw);
 }
 
-template <class SC, int C>
+template <class SC, int C, bool STREAMED = false>
 constexpr SchedDesc make_cluster_desc(const char* name) {
     return SchedDesc{name,
                      ClusterGeom<SC, C>::N,
@@ -268,9 +360,9 @@ constexpr SchedDesc make_cluster_desc(const char* name) {
                      SC::TW_ELEMS + ClusterGeom<SC, C>::N,
                      SC::RL,
                      0,
-                     &launch_cluster_fused<SC, C>,
+                     STREAMED ? &launch_cluster_streamed<SC, C> : &launch_cluster_fused<SC, C>,
                      &launch_cluster_dft<SC, C>,
-                     &prepare_cluster<SC, C>,
+                     STREAMED ? &prepare_cluster_streamed<SC, C> : &prepare_cluster<SC, C>,
                      nullptr,
                      0,
                      nullptr,
@@ -280,6 +372,12 @@ constexpr SchedDesc make_cluster_desc(const char* name) {
 using M8192 = Sched<8192, 32, 16, 16, 32>;      // 256 threads, 66 KiB of shared memory per block
 using M16384 = Sched<16384, 32, 16, 32, 32>;    // 512 threads, 132 KiB
 const SchedDesc kTable[] = {
+    make_cluster_desc<M8192, 4, true>("n32768_c4_m8192_e32_sr"),
+    make_cluster_desc<M16384, 2, true>("n32768_c2_m16384_e32_sr"),
+    make_cluster_desc<M8192, 8, true>("n65536_c8_m8192_e32_sr"),
+    make_cluster_desc<M16384, 4, true>("n65536_c4_m16384_e32_sr"),
+    make_cluster_desc<M16384, 8, true>("n131072_c8_m16384_e32_sr"),
+    make_cluster_desc<M8192, 16, true>("n131072_c16_m8192_e32_sr"),
     make_cluster_desc<M8192, 4>("n32768_c4_m8192_e32"),
     make_cluster_desc<M16384, 2>("n32768_c2_m16384_e32"),
     make_cluster_desc<M8192, 8>("n65536_c8_m8192_e32"),

@@ -76,9 +76,9 @@ def test_lfm_spectrum_long(sar, orc, n):
     assert M.rel_l2(H.cpu().numpy(), ref) < FFT_TOL
 
 
-CLUSTER_SCHEDULES = [(32768, "n32768_c4_m8192_e32"), (32768, "n32768_c2_m16384_e32"),
-                     (65536, "n65536_c8_m8192_e32"), (65536, "n65536_c4_m16384_e32"),
-                     (131072, "n131072_c8_m16384_e32"), (131072, "n131072_c16_m8192_e32")]
+CLUSTER_SCHEDULES = [(n, f"n{n}_c{c}_m{m}_e32{v}") for (n, c, m) in
+                     [(32768, 4, 8192), (32768, 2, 16384), (65536, 8, 8192), (65536, 4, 16384),
+                      (131072, 8, 16384), (131072, 16, 8192)] for v in ("", "_sr")]
 
 
 def test_cluster_schedule_list_is_complete(sar):
