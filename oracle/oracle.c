@@ -26,7 +26,12 @@
  * The FFT is a textbook iterative radix-2 decimation-in-time transform.  Each
  * twiddle factor exp(sign * 2 pi i j / len) is evaluated directly with cos()
  * and sin() for its own index j -- never by a recurrence -- so its error does
- * not grow with the transform length.
+ * not grow with the transform length.  A length that is not a power of two
+ * takes the O(n^2) sum of the DFT's definition instead, with the twiddle of
+ * exponent j*k read from a table of the n roots (entry (j*k) mod n, each
+ * evaluated by cos() and sin() of its own index); every function built on the
+ * transform (matched filter, line and scene compression) then holds for any
+ * length as the same definitions at that length.
  *
  * Data layout: complex numbers are pairs of doubles (re, im), i.e. the
  * memory layout of C99 double complex and of numpy.complex128.  Matrices are
@@ -60,12 +65,47 @@ static int is_pow2(int64_t n) { return n >= 1 && (n & (n - 1)) == 0; }
 /* Discrete Fourier transform (definition:  X[k] = sum_n x[n] e^{sign 2 pi i n k / N}). */
 /* ------------------------------------------------------------------------ */
 
-/* In-place unnormalised radix-2 FFT of length n (a power of two).
+/* The DFT of any length n >= 1 by its definition, in place:
+ * X[k] = sum_j x[j] w[(j k) mod n], w[m] = e^{sign 2 pi i m / n}. */
+static int oracle_dft(int64_t n, cplx *x, int sign)
+{
+    cplx *w = (cplx *)malloc(sizeof(cplx) * (size_t)n);
+    cplx *y = (cplx *)malloc(sizeof(cplx) * (size_t)n);
+    if (!w || !y) {
+        free(w);
+        free(y);
+        return -1;
+    }
+    for (int64_t m = 0; m < n; ++m) {
+        double ang = (double)sign * kTwoPi * (double)m / (double)n;
+        w[m] = cos(ang) + I * sin(ang);
+    }
+    for (int64_t k = 0; k < n; ++k) {
+        cplx acc = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            int64_t e = (j * k) % n;
+#if ORACLE_PLANT == 9
+            e = (j * k) & (n - 1); /* planted: exponent reduced as if n were a power of two */
+#endif
+            acc += x[j] * w[e];
+        }
+        y[k] = acc;
+    }
+    memcpy(x, y, sizeof(cplx) * (size_t)n);
+    free(w);
+    free(y);
+    return 0;
+}
+
+/* In-place unnormalised DFT of length n: the radix-2 FFT when n is a power
+ * of two, the definition's O(n^2) sum otherwise.
  * sign = -1: forward transform; sign = +1: inverse kernel (no 1/N). */
 int oracle_fft(int64_t n, cplx *x, int sign)
 {
-    if (!is_pow2(n) || (sign != 1 && sign != -1) || (n > 0 && !x))
+    if (n < 1 || (sign != 1 && sign != -1) || !x)
         return -1;
+    if (!is_pow2(n))
+        return oracle_dft(n, x, sign);
 #if ORACLE_PLANT == 1
     sign = -sign; /* planted: wrong exponent sign */
 #endif
@@ -110,7 +150,7 @@ int oracle_fft(int64_t n, cplx *x, int sign)
  * centred on index 0) and sits at position m mod n of a length-n line. */
 int oracle_matched_filter(int64_t n, int64_t n_chirp, const cplx *chirp, cplx *H)
 {
-    if (!is_pow2(n) || n_chirp < 1 || n_chirp > n || !chirp || !H)
+    if (n < 1 || n_chirp < 1 || n_chirp > n || !chirp || !H)
         return -1;
     memset(H, 0, sizeof(cplx) * (size_t)n);
     for (int64_t j = 0; j < n_chirp; ++j) {
@@ -139,7 +179,7 @@ int oracle_matched_filter(int64_t n, int64_t n_chirp, const cplx *chirp, cplx *H
 /* One line of length n, in place. */
 int oracle_compress_line(int64_t n, cplx *x, const cplx *H)
 {
-    if (!is_pow2(n) || !x || !H)
+    if (n < 1 || !x || !H)
         return -1;
     if (oracle_fft(n, x, -1))
         return -1;
@@ -177,7 +217,7 @@ static void *line_worker(void *arg)
  * the thread count. */
 int oracle_compress_lines(int64_t n_lines, int64_t n, cplx *data, const cplx *H, int nthreads)
 {
-    if (n_lines < 0 || !is_pow2(n) || (n_lines > 0 && !data) || !H)
+    if (n_lines < 0 || n < 1 || (n_lines > 0 && !data) || !H)
         return -1;
     if (nthreads < 1)
         nthreads = 1;
@@ -234,15 +274,14 @@ int oracle_corner_turn(int64_t rows, int64_t cols, const cplx *in, cplx *out)
  * Hr:    range filter spectrum, n_range values.
  * Ha:    azimuth filter spectrum, l_az values.
  * image: n_range x n_az output (range-bin-major rows).
- * l_az:  azimuth transform length (a power of two >= n_az).  When n_az is
+ * l_az:  azimuth transform length (>= n_az).  When n_az is
  *        smaller the azimuth lines are zero-padded to l_az before the FFT and
  *        cropped back to n_az after the IFFT (circular correlation at length
  *        l_az).  With l_az == n_az this is the plain three-step algorithm. */
 int oracle_rda(int64_t n_az, int64_t n_range, int64_t l_az, const cplx *raw, const cplx *Hr,
                const cplx *Ha, cplx *image, int nthreads)
 {
-    if (n_az < 1 || !is_pow2(n_range) || !is_pow2(l_az) || l_az < n_az || !raw || !Hr || !Ha ||
-        !image)
+    if (n_az < 1 || n_range < 1 || l_az < n_az || !raw || !Hr || !Ha || !image)
         return -1;
     cplx *work = (cplx *)malloc(sizeof(cplx) * (size_t)(n_az * n_range));
     cplx *az = (cplx *)calloc((size_t)(n_range * l_az), sizeof(cplx));

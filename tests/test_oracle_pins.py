@@ -7,7 +7,10 @@ builds of ``oracle.c`` and check that at least one of them fails.
 What pins what:
 * fft                -- numpy.fft (library routine), the O(N^2) DFT matrix
                         written from the definition, round trip, Parseval,
-                        linearity.
+                        linearity; lengths that are not powers of two
+                        (3, 5, 6, 7, 12, 96, 100, 1000) against numpy.fft.
+* compress_lines, rda at lengths that are not powers of two -- the circulant
+                        matrix products at those lengths.
 * matched_filter     -- direct O(N*Nc) DFT sum of the centred chirp.
 * compress_lines     -- circular cross-correlation with the centred chirp,
                         written as a circulant matrix product (no FFT).
@@ -78,6 +81,35 @@ def pin_fft_numpy(o):
             got = o.fft(x, inverse=inv)
             err = np.max(np.abs(got - ref)) / max(1.0, np.max(np.abs(ref)))
             assert err < 1e-13, (n, inv, err)
+
+
+def pin_fft_any_length(o):
+    """Lengths that are not powers of two take the definition's O(n^2) sum."""
+    for n in [3, 5, 6, 7, 12, 96, 100, 1000]:
+        x = crand(n)
+        for inv in (False, True):
+            ref = np.fft.ifft(x) * n if inv else np.fft.fft(x)
+            got = o.fft(x, inverse=inv)
+            err = np.max(np.abs(got - ref)) / max(1.0, np.max(np.abs(ref)))
+            assert err < 1e-12, (n, inv, err)
+
+
+def pin_compress_any_length(o):
+    """Line and scene compression at lengths that are not powers of two: the
+    circular correlation at that length, as circulant matrix products."""
+    for n, (nc, tbp) in [(100, (24, 8.0)), (96, (32, 16.0)), (300, (40, 20.0))]:
+        c = sarsim.lfm_chirp(nc, tbp)
+        H = o.matched_filter(n, c)
+        x = crand(3, n)
+        ref = x @ circulant_corr_matrix(c, n)
+        got = o.compress_lines(x, H)
+        assert np.max(np.abs(got - ref)) < 1e-11 * np.max(np.abs(ref)), n
+    n_az, n_r = 90, 150
+    ca, cr = sarsim.lfm_chirp(20, 6.0), sarsim.lfm_chirp(30, 10.0)
+    raw = crand(n_az, n_r)
+    img = o.rda(raw, o.matched_filter(n_r, cr), o.matched_filter(n_az, ca))
+    ref = (circulant_corr_matrix(ca, n_az).T @ raw @ circulant_corr_matrix(cr, n_r)).T
+    assert M.rel_l2(img, ref) < 1e-13
 
 
 def pin_fft_dft_matrix(o):
@@ -243,7 +275,8 @@ def pin_rda_full_point_target(o):
     assert abs(plain).max() < 0.8 * abs(img[n0, a0])
 
 
-ALL_PINS = [pin_fft_numpy, pin_fft_dft_matrix, pin_fft_identities, pin_matched_filter,
+ALL_PINS = [pin_fft_numpy, pin_fft_any_length, pin_compress_any_length, pin_fft_dft_matrix, pin_fft_identities,
+            pin_matched_filter,
             pin_compress_lines_circulant, pin_corner_turn, pin_rda_bruteforce,
             pin_point_target_peaks, pin_impulse_response, pin_rcmc_bandlimited_shift, pin_rda_full_point_target]
 
@@ -320,7 +353,7 @@ def test_rel_l2_and_peak_tiebreak():
 # planted mistakes: every deliberately broken oracle must fail a pin
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("plant", [1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("plant", [1, 2, 3, 4, 5, 6, 7, 8, 9])
 def test_planted_mistake_is_caught(plant, tmp_path):
     path = oracle.build(str(tmp_path / f"liboracle_plant{plant}.so"), plant=plant, force=True)
     o = oracle.Oracle(oracle.load(path))
