@@ -28,7 +28,8 @@
  *     device surfaces on a later call or on sar_sync().  sar_last_error()
  *     gives a message for the calling thread's last failure.
  *   - No C++ exception crosses this interface.
- *   - Supported line lengths: powers of two from 256 to 131072.  Lines up to
+ *   - Plans take any line length in [2, 8192] (see sar_plan_create); the
+ *     other entry points take powers of two from 256 to 131072.  Lines up to
  *     16384 samples run one line per thread block; longer lines run one line
  *     per thread-block cluster of 2 to 16 blocks exchanging it through
  *     distributed shared memory (sar_range_compress, sar_azimuth_compress,
@@ -100,7 +101,12 @@ typedef struct {
 
 /* Create a plan for an n_az x n_range scene (Sec. IV-A, the N_a x N_r data
  * matrix).  n_range and n_az: powers of two in [256, 131072] (above 16384 on
- * thread-block clusters, without the folded corner turn).  Allocates the
+ * thread-block clusters, without the folded corner turn), or any other length
+ * in [2, 8192]: such lines get the exact length-n compression
+ * IFFT_n(FFT_n(x) . H) through a zero-padded linear convolution at the
+ * power-of-two length L >= 2n - 1 (filter FFT_L(IFFT_n(H)) designed in FP64 at
+ * plan time), one fused launch per pass as for powers of two; the unfused
+ * pipeline and split precision need powers of two.  Allocates the
  * plan's device tables on the current device, builds them (FP64 twiddle
  * phases rounded to FP32) and synchronises the device once; not for the hot
  * loop.  *out receives the plan, or NULL on failure. */

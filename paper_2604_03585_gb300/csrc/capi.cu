@@ -51,6 +51,25 @@ sar_status check_length(int64_t n, const char *what) {
     return SAR_OK;
 }
 
+// A plan's line length: a power of two in [256, 131072] (the line engine at
+// that length), or any other length in [2, 8192] (the zero-padded linear
+// convolution at L = max(256, next power of two >= 2n - 1), wrap_line.cu).
+bool native_length(int64_t n) { return is_pow2(n) && n >= 256 && n <= 131072; }
+
+sar_status check_plan_length(int64_t n, const char *what) {
+    if (n < 1) return fail(SAR_ERR_INVALID_ARG, "%s = %lld must be >= 1", what, (long long)n);
+    if (native_length(n) || (n >= 2 && n <= 8192)) return SAR_OK;
+    return fail(SAR_ERR_UNSUPPORTED,
+                "%s = %lld: supported lengths are powers of two in [256, 131072] and any length in [2, 8192]", what,
+                (long long)n);
+}
+
+int64_t wrap_length(int64_t n) {
+    int64_t L = 256;
+    while (L < 2 * n - 1) L <<= 1;
+    return L;
+}
+
 // A compute pointer must be non-null, 16-byte aligned and device-accessible
 // memory of the current device (a host pointer handed to a kernel would
 // fault the GPU, so it is refused here).
@@ -76,7 +95,8 @@ size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct LinePlan {
     const SchedDesc *sched = nullptr;
-    float2 *filt = nullptr;  // n complex, register order, 1/N folded in
+    int64_t n = 0;           // line length (sched->n unless the length is not a power of two)
+    float2 *filt = nullptr;  // sched->n complex, register order, 1/sched->n folded in
     float2 *tw = nullptr;    // twiddle tables
     float2 *filt_nat = nullptr;  // n complex, natural order, 1/N folded in (unfused path)
 };
@@ -185,8 +205,11 @@ sar_status sar_plan_create_ex(int64_t n_range, int64_t n_az, const sar_filters *
     *out = nullptr;
     if (!filters) return fail(SAR_ERR_INVALID_ARG, "filters is NULL");
     sar_status st;
-    if ((st = check_length(n_range, "n_range")) != SAR_OK) return st;
-    if ((st = check_length(n_az, "n_az")) != SAR_OK) return st;
+    if ((st = check_plan_length(n_range, "n_range")) != SAR_OK) return st;
+    if ((st = check_plan_length(n_az, "n_az")) != SAR_OK) return st;
+    const bool wrap_r = !native_length(n_range), wrap_a = !native_length(n_az);
+    if ((wrap_r && range_schedule) || (wrap_a && az_schedule))
+        return fail(SAR_ERR_INVALID_ARG, "schedules can be named only for power-of-two lengths");
     if (filters->flags & ~SAR_PLAN_UNFOLDED_CORNER_TURN)
         return fail(SAR_ERR_INVALID_ARG, "filters->flags has unknown bits 0x%x", filters->flags);
     const int prec = filters->precision;
@@ -199,13 +222,16 @@ sar_status sar_plan_create_ex(int64_t n_range, int64_t n_az, const sar_filters *
     if ((st = check_device_ptr(filters->range_spectrum, "filters->range_spectrum")) != SAR_OK) return st;
     if ((st = check_device_ptr(filters->az_spectrum, "filters->az_spectrum")) != SAR_OK) return st;
 
-    const bool want_fold = !(filters->flags & SAR_PLAN_UNFOLDED_CORNER_TURN) && prec == SAR_PREC_FP32;
+    const bool want_fold = !(filters->flags & SAR_PLAN_UNFOLDED_CORNER_TURN) && prec == SAR_PREC_FP32 && !wrap_r;
     const SchedDesc *dr = range_schedule ? sar::find_schedule(range_schedule) : nullptr;
-    if (!range_schedule) {
+    if (wrap_r) {
+        dr = sar::wrap_schedule((int)wrap_length(n_range));
+    } else if (!range_schedule) {
         dr = want_fold ? sar::default_ct_schedule((int)n_range) : nullptr;
         if (!dr || n_az % dr->ct_lines) dr = sar::default_schedule((int)n_range);
     }
-    const SchedDesc *da = az_schedule ? sar::find_schedule(az_schedule) : sar::default_schedule((int)n_az);
+    const SchedDesc *da = wrap_a ? sar::wrap_schedule((int)wrap_length(n_az))
+                                 : az_schedule ? sar::find_schedule(az_schedule) : sar::default_schedule((int)n_az);
     if (range_schedule && (!dr || dr->n != n_range))
         return fail(SAR_ERR_INVALID_ARG, "range schedule '%s' is unknown or not for n_range", range_schedule);
     if (az_schedule && (!da || da->n != n_az))
@@ -224,16 +250,18 @@ sar_status sar_plan_create_ex(int64_t n_range, int64_t n_az, const sar_filters *
     cudaGetDevice(&p->device);
     p->range.sched = dr;
     p->az.sched = da;
+    p->range.n = n_range;
+    p->az.n = n_az;
     p->prec = prec;
     p->fold = want_fold && dr->fused_ct && n_az % dr->ct_lines == 0;
 
-    // one block: filt_r | tw_r | filt_a | tw_a | idx (int32, max n)
+    // one block: filt_r | tw_r | filt_a | tw_a | idx (int32, max engine length) | status | filt_nat_r | filt_nat_a
     const size_t o_fr = 0;
-    const size_t o_tr = o_fr + align_up(sizeof(float2) * (size_t)n_range);
+    const size_t o_tr = o_fr + align_up(sizeof(float2) * (size_t)dr->n);
     const size_t o_fa = o_tr + align_up(sizeof(float2) * (size_t)dr->tw_elems);
-    const size_t o_ta = o_fa + align_up(sizeof(float2) * (size_t)n_az);
+    const size_t o_ta = o_fa + align_up(sizeof(float2) * (size_t)da->n);
     const size_t o_ix = o_ta + align_up(sizeof(float2) * (size_t)da->tw_elems);
-    const size_t o_st = o_ix + align_up(sizeof(int32_t) * (size_t)(n_range > n_az ? n_range : n_az));
+    const size_t o_st = o_ix + align_up(sizeof(int32_t) * (size_t)(dr->n > da->n ? dr->n : da->n));
     const size_t o_nr = o_st + 256;
     const size_t o_na = o_nr + align_up(sizeof(float2) * (size_t)n_range);
     const size_t total = o_na + align_up(sizeof(float2) * (size_t)n_az);
@@ -257,8 +285,10 @@ sar_status sar_plan_create_ex(int64_t n_range, int64_t n_az, const sar_filters *
 
     cudaStream_t s = nullptr;
     std::vector<int32_t> idx;
+    void *wrap_tmp = nullptr;   // plan-time scratch of the filters of non-power-of-two lengths
     auto cleanup_fail = [&](cudaError_t err, const char *what) {
         if (s) cudaStreamDestroy(s);
+        if (wrap_tmp) cudaFree(wrap_tmp);
         cudaFree(p->block);
         delete p;
         return cuda_fail(err, what);
@@ -275,6 +305,7 @@ sar_status sar_plan_create_ex(int64_t n_range, int64_t n_az, const sar_filters *
     } dims[2] = {{&p->range, filters->range_spectrum}, {&p->az, filters->az_spectrum}};
     for (auto &dm : dims) {
         const SchedDesc &d = *dm.lp->sched;
+        const int64_t n = dm.lp->n;
         if ((e = d.prepare()) != cudaSuccess) return cleanup_fail(e, "cudaFuncSetAttribute");
         if ((e = sar::build_twiddles(d, dm.lp->tw, s)) != cudaSuccess) return cleanup_fail(e, "twiddle tables");
         idx.assign(d.n, 0);
@@ -282,9 +313,24 @@ sar_status sar_plan_create_ex(int64_t n_range, int64_t n_az, const sar_filters *
         if ((e = cudaMemcpyAsync(idx_dev, idx.data(), sizeof(int32_t) * d.n, cudaMemcpyHostToDevice, s)) !=
             cudaSuccess)
             return cleanup_fail(e, "filter index copy");
-        if ((e = sar::build_filter(d, (const float2 *)dm.H, dm.lp->filt, idx_dev, s)) != cudaSuccess)
+        const float2 *spectrum = (const float2 *)dm.H;
+        if (n != d.n) {
+            // length n that is not a power of two: the engine's filter is
+            // G = FFT_L(IFFT_n(H) zero-padded to L), L = d.n
+            const size_t scratch = sar::wrap_filter_scratch_bytes((int)n, d.n);
+            if ((e = cudaMalloc(&wrap_tmp, scratch + sizeof(float2) * (size_t)d.n)) != cudaSuccess) {
+                wrap_tmp = nullptr;
+                cudaGetLastError();
+                return cleanup_fail(e, "filter design scratch");
+            }
+            float2 *G = (float2 *)((char *)wrap_tmp + scratch);
+            if ((e = sar::build_wrap_filter(spectrum, (int)n, d.n, wrap_tmp, G, s)) != cudaSuccess)
+                return cleanup_fail(e, "filter design");
+            spectrum = G;
+        }
+        if ((e = sar::build_filter(d, spectrum, dm.lp->filt, idx_dev, s)) != cudaSuccess)
             return cleanup_fail(e, "filter permutation");
-        if ((e = sar::build_natural_filter((const float2 *)dm.H, dm.lp->filt_nat, d.n, s)) != cudaSuccess)
+        if (n == d.n && (e = sar::build_natural_filter(spectrum, dm.lp->filt_nat, d.n, s)) != cudaSuccess)
             return cleanup_fail(e, "natural-order filter");
         if (prec != SAR_PREC_FP32) {
             // position-order filter of the tensor-core kernel, in place of the
@@ -298,6 +344,10 @@ sar_status sar_plan_create_ex(int64_t n_range, int64_t n_az, const sar_filters *
                 return cleanup_fail(e, "filter permutation");
         }
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cleanup_fail(e, "plan tables");
+        if (wrap_tmp) {
+            cudaFree(wrap_tmp);
+            wrap_tmp = nullptr;
+        }
     }
     cudaStreamDestroy(s);
     *out = p;
@@ -458,7 +508,7 @@ static sar_status run_fused(const sar_plan_s *p, const LinePlan &lp, int64_t n_l
         if (e != cudaSuccess) return cuda_fail(e, what);
         return SAR_OK;
     }
-    cudaError_t e = d.fused((const float2 *)in, (float2 *)out, n_lines, d.n, d.n, lp.filt, lp.tw, p->ctl, s);
+    cudaError_t e = d.fused((const float2 *)in, (float2 *)out, n_lines, lp.n, (int)lp.n, lp.filt, lp.tw, p->ctl, s);
     if (e != cudaSuccess) return cuda_fail(e, what);
     return SAR_OK;
 }
@@ -582,8 +632,14 @@ sar_status sar_rda_process_oop(sar_plan p, const void *raw, void *work, void *im
 // replaces): forward FFT kernel, spectrum multiply kernel, inverse FFT
 // kernel, each reading and writing the whole line set (six transfers per
 // line instead of two).
+static bool unfused_ok(const LinePlan &lp) { return lp.n == lp.sched->n && lp.sched->dft; }
+static sar_status unfused_refusal() {
+    return fail(SAR_ERR_UNSUPPORTED, "the unfused pipeline needs power-of-two line lengths");
+}
+
 static sar_status run_unfused(const sar_plan_s *p, const LinePlan &lp, int64_t n_lines, void *data, cudaStream_t s) {
     const SchedDesc &d = *lp.sched;
+    if (!unfused_ok(lp)) return unfused_refusal();
     float2 *tw = nullptr;
     sar_status st = cached_twiddles(&d, &tw);
     if (st != SAR_OK) return st;
@@ -616,6 +672,7 @@ sar_status sar_rda_process_unfused(sar_plan p, void *raw, void *image, sar_strea
     if ((st = check_device_ptr(image, "image")) != SAR_OK) return st;
     if (overlaps(raw, image, sizeof(float2) * (size_t)(p->n_az * p->n_range)))
         return fail(SAR_ERR_INVALID_ARG, "raw and image overlap");
+    if (!unfused_ok(p->range) || !unfused_ok(p->az)) return unfused_refusal();
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = run_unfused(p, p->range, p->n_az, raw, s)) != SAR_OK) return st;
     cudaError_t e = sar::launch_transpose((const float2 *)raw, (float2 *)image, p->n_az, p->n_range, s);

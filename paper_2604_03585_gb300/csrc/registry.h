@@ -63,6 +63,10 @@ const SchedDesc *default_schedule(int n);
 void set_preferred_schedule(const SchedDesc *d);
 const SchedDesc *default_ct_schedule(int n);
 void set_preferred_ct_schedule(const SchedDesc *d);
+// The schedule that compresses lines of a length n that is not a power of two
+// at the engine length L (a power of two >= 2n - 1), or nullptr.  Not part of
+// the enumeration below.
+const SchedDesc *wrap_schedule(int L);
 // Schedule by name, or nullptr.
 const SchedDesc *find_schedule(const char *name);
 // Visit every schedule.

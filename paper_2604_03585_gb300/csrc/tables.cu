@@ -84,6 +84,65 @@ cudaError_t spectrum_multiply(float2 *data, const float2 *h, int64_t n_lines, in
     return cudaGetLastError();
 }
 
+// --- filter of a line length that is not a power of two -------------------
+// roots[e] = exp(sign 2 pi i e / m), e < m, FP64.
+__global__ void roots_f64_kernel(double2 *roots, int m, int sign) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m) return;
+    double s, c;
+    sincospi((double)sign * 2.0 * (double)e / (double)m, &s, &c);
+    roots[e] = make_double2(c, s);
+}
+
+// out[j] = scale * sum_{q < n_in} in[q] roots[(j q) mod m], FP64, one warp per
+// output j < n_out; in is complex64 (IN_F32) or complex128.
+template <bool IN_F32>
+__global__ void dft_f64_kernel(const void *in_, int n_in, const double2 *roots, int m, int n_out, double scale,
+                               double2 *out64, float2 *out32) {
+    const int j = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (j >= n_out) return;
+    double re = 0.0, im = 0.0;
+    for (int q = lane; q < n_in; q += 32) {
+        double xr, xi;
+        if (IN_F32) {
+            const float2 v = ((const float2 *)in_)[q];
+            xr = v.x;
+            xi = v.y;
+        } else {
+            const double2 v = ((const double2 *)in_)[q];
+            xr = v.x;
+            xi = v.y;
+        }
+        const double2 w = roots[((int64_t)j * q) % m];
+        re = fma(xr, w.x, fma(-xi, w.y, re));
+        im = fma(xr, w.y, fma(xi, w.x, im));
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        re += __shfl_down_sync(0xffffffffu, re, o);
+        im += __shfl_down_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) {
+        if (out64) out64[j] = make_double2(re * scale, im * scale);
+        if (out32) out32[j] = make_float2((float)(re * scale), (float)(im * scale));
+    }
+}
+
+size_t wrap_filter_scratch_bytes(int n, int L) { return sizeof(double2) * ((size_t)2 * n + (size_t)L); }
+
+// G = FFT_L(h zero-padded to L), h = IFFT_n(H), both by their definitions in
+// FP64 (plan time, O(n L)), G rounded once to FP32.  scratch holds
+// wrap_filter_scratch_bytes(n, L) bytes.
+cudaError_t build_wrap_filter(const float2 *H, int n, int L, void *scratch, float2 *G, cudaStream_t st) {
+    double2 *roots_n = (double2 *)scratch, *h = roots_n + n, *roots_L = h + n;
+    roots_f64_kernel<<<(n + 255) / 256, 256, 0, st>>>(roots_n, n, +1);
+    roots_f64_kernel<<<(L + 255) / 256, 256, 0, st>>>(roots_L, L, -1);
+    dft_f64_kernel<true><<<(n + 7) / 8, 256, 0, st>>>(H, n, roots_n, n, n, 1.0 / (double)n, h, nullptr);
+    dft_f64_kernel<false><<<(L + 7) / 8, 256, 0, st>>>(h, n, roots_L, L, L, 1.0, nullptr, G);
+    return cudaGetLastError();
+}
+
 cudaError_t build_natural_filter(const float2 *H, float2 *dst, int n, cudaStream_t st) {
     scale_copy_kernel<<<(n + 255) / 256, 256, 0, st>>>(dst, H, n, 1.0f / (float)n);
     return cudaGetLastError();

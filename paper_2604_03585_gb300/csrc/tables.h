@@ -26,6 +26,9 @@ cudaError_t launch_rcmc(int taps, const float2 *in, float2 *out, int n_range, in
                         double r_near, int staged_rows, cudaStream_t st);
 int rcmc_staged_rows(int n_range, int n_f, double r_near, const void *host_cols);
 void rd_columns(int n_f, double kappa, double vs, void *host_cols);
+// lines whose length is not a power of two (zero-padded linear convolution)
+size_t wrap_filter_scratch_bytes(int n, int L);
+cudaError_t build_wrap_filter(const float2 *H, int n, int L, void *scratch, float2 *G, cudaStream_t st);
 size_t rd_column_bytes();
 int corner_turn_variant();
 }  // namespace sar

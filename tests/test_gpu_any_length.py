@@ -1,0 +1,148 @@
+"""GPU: line lengths that are not powers of two (2 ... 8192) against the FP64
+oracle, whose transform at such lengths is the DFT's definition: the exact
+length-n compression y = IFFT_n(FFT_n(x) . H) (Sec. II-B) and the scene
+compression (Sec. IV-A) at those lengths."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import sarsim
+from oracle import metrics as M
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+NTHREADS = max(1, os.cpu_count() or 1)
+LINE_TOL = 4e-6
+SCENE_TOL = 2e-5
+
+
+@pytest.fixture(scope="module")
+def sar(built_lib):
+    import paper_2604_03585_gb300 as sar
+    assert torch.cuda.is_available(), "gpu tests need a CUDA device"
+    torch.cuda.set_device(0)
+    return sar
+
+
+@pytest.fixture(scope="module")
+def orc():
+    return oracle.default()
+
+
+def noise(seed, rows, n):
+    return sarsim.complex_gaussian(seed, 0, rows * n, 1.0).reshape(rows, n)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex64)).cuda()
+
+
+# n, lines: every engine length L = max(256, next pow2 >= 2n - 1) from 256 to
+# 16384, the smallest and largest n of several of them, and n = 2
+@pytest.mark.parametrize("n,lines", [(2, 5), (3, 7), (100, 9), (128, 9), (129, 9), (255, 9), (257, 6), (500, 6),
+                                     (1000, 5), (1023, 5), (1500, 4), (2049, 3), (3000, 3), (4095, 3), (5000, 2),
+                                     (8191, 2)])
+def test_line_compression_any_length(sar, orc, n, lines):
+    x = noise(31 + n, lines, n)
+    nc = max(1, n // 4)
+    H = orc.matched_filter(n, sarsim.lfm_chirp(nc, nc / 2.0))
+    ref = orc.compress_lines(x, H, nthreads=NTHREADS)
+    dummy = dev(np.ones(lines))
+    plan = sar.sar_plan_create(n, lines, dev(H), dummy)
+    got_d = dev(x)
+    sar.sar_range_compress(plan, got_d)
+    torch.cuda.synchronize()
+    got = got_d.cpu().numpy()
+    # any spectrum, out of place as well (not a matched filter: no symmetry to hide behind)
+    Hr = noise(7, 1, n)[0]
+    ref2 = orc.compress_lines(x, Hr, nthreads=NTHREADS)
+    plan2 = sar.sar_plan_create(n, lines, dev(Hr), dummy)
+    xd = dev(x)
+    out = torch.empty_like(xd)
+    sar.sar_range_compress_oop(plan2, xd, out)
+    torch.cuda.synchronize()
+    got2 = out.cpu().numpy()
+    assert np.array_equal(xd.cpu().numpy(), x.astype(np.complex64))
+    L = sar.sar_plan_get_schedules(plan)[0]["n"]
+    plan.destroy()
+    plan2.destroy()
+    e1, e2 = M.rel_l2(got, ref), M.rel_l2(got2, ref2)
+    print(f"\nANY n={n} (L={L}): matched {e1:.2e}, random H {e2:.2e}")
+    assert L == max(256, 1 << (2 * n - 2).bit_length())
+    assert e1 < LINE_TOL and e2 < LINE_TOL
+
+
+@pytest.mark.parametrize("n_az,n_range", [(300, 1000), (256, 3000), (1000, 256), (300, 4096), (33, 77)])
+def test_scene_any_length_vs_oracle(sar, orc, n_az, n_range):
+    """Scene compression with lengths that are not powers of two in either
+    dimension (300 x 4096 folds the corner turn into the range pass with
+    image rows of 300 samples)."""
+    (ncr, tbr), _ = sarsim.scaled_chirps(n_range, 256)
+    nca = max(4, n_az // 4)
+    tba = max(1.0, nca / 8.0)
+    targets = [(n_az // 4, n_range // 3), (3 * n_az // 4, 2 * n_range // 3)]
+    if n_az < 100:   # one target: two would share each other's peak-search window
+        targets = [(n_az // 2, n_range // 2)]
+    spec = sarsim.SceneSpec(n_az=n_az, n_range=n_range, targets=targets, range_chirp=(ncr, tbr),
+                            az_chirp=(nca, tba), snr_db=20.0, seed=8)
+    raw = sarsim.echo(spec)
+    Hr = orc.matched_filter(n_range, sarsim.lfm_chirp(ncr, tbr))
+    Ha = orc.matched_filter(n_az, sarsim.lfm_chirp(nca, tba))
+    ref = orc.rda(raw, Hr, Ha, nthreads=NTHREADS)
+    plan = sar.sar_plan_create(n_range, n_az, dev(Hr), dev(Ha))
+    img = torch.empty((n_range, n_az), dtype=torch.complex64, device="cuda")
+    raw_d = dev(raw)
+    sar.sar_rda_process(plan, raw_d, img)
+    torch.cuda.synchronize()
+    got = img.cpu().numpy()
+    folded = sar.sar_plan_folds_corner_turn(plan)
+    plan.destroy()
+    err = M.rel_l2(got, ref)
+    print(f"\nANY scene {n_az}x{n_range}: rel_l2 {err:.2e} folded={folded}")
+    assert err < SCENE_TOL
+    for (a0, r0) in targets:
+        assert M.peak(got, (r0, a0)) == M.peak(ref, (r0, a0)) == (r0, a0)
+    if n_range == 4096 and n_az % 4 == 0:
+        assert folded
+
+
+def test_schedules_of_any_length_plans(sar):
+    a, b = dev(np.ones(1000)), dev(np.ones(300))
+    plan = sar.sar_plan_create(1000, 300, a, b)
+    r, z = sar.sar_plan_get_schedules(plan)
+    assert r["n"] == 2048 and r["name"].startswith("wrap_")
+    assert z["n"] == 1024 and z["name"].startswith("wrap_")
+    assert not sar.sar_plan_folds_corner_turn(plan)
+    plan.destroy()
+    # wrap schedules are not part of the enumeration (and so never autotuned)
+    assert not [d for d in sar.schedules() if d["name"].startswith("wrap_")]
+
+
+def test_any_length_refusals(sar):
+    a, b = dev(np.ones(1000)), dev(np.ones(256))
+    with pytest.raises(sar.SarError) as e:
+        sar.sar_plan_create(8193, 256, dev(np.ones(8193)), b)
+    assert e.value.status == sar.SAR_ERR_UNSUPPORTED
+    with pytest.raises(sar.SarError) as e:
+        sar.sar_plan_create_ex(1000, 256, a, b, range_schedule="n1024_e32_r32x32_l4")
+    assert e.value.status == sar.SAR_ERR_INVALID_ARG
+    plan = sar.sar_plan_create(1000, 256, a, b)
+    x = torch.zeros((256, 1000), dtype=torch.complex64, device="cuda")
+    img = torch.empty((1000, 256), dtype=torch.complex64, device="cuda")
+    for call in (lambda: sar.sar_range_compress_unfused(plan, x),
+                 lambda: sar.sar_rda_process_unfused(plan, x, img)):
+        with pytest.raises(sar.SarError) as e:
+            call()
+        assert e.value.status == sar.SAR_ERR_UNSUPPORTED
+    sar.sar_rda_process(plan, x, img)      # the fused path runs
+    torch.cuda.synchronize()
+    assert float(img.abs().max()) == 0.0
+    plan.destroy()
+    plan = sar.sar_plan_create(256, 1000, b, a)
+    sar.sar_plan_set_geometry(plan, 10.0, 0.3, 100.0, 16)
+    with pytest.raises(sar.SarError) as e:
+        sar.sar_rda_full(plan, x, torch.empty_like(img), torch.empty_like(img))
+    assert e.value.status == sar.SAR_ERR_UNSUPPORTED
+    plan.destroy()

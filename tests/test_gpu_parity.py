@@ -466,7 +466,7 @@ def test_bad_arguments_are_refused(sar):
         sar.sar_rda_process(plan, good, good)                # image overlaps raw
     assert e.value.status == sar.SAR_ERR_INVALID_ARG
     with pytest.raises(sar.SarError) as e:
-        sar.sar_plan_create(256, 256 * 3, Hr, Ha)
+        sar.sar_plan_create(256, 256 * 33, Hr, Ha)          # not a power of two and above 8192
     assert e.value.status == sar.SAR_ERR_UNSUPPORTED
     with pytest.raises(sar.SarError) as e:
         sar.sar_plan_create(256, 262144, Hr, Ha)
