@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--azimuth-schedule", default=None, help="schedule of the azimuth pass (default: autotuned)")
     ap.add_argument("--no-autotune", action="store_true", help="use the compiled-in preferred schedules")
     ap.add_argument("--no-extras", action="store_true", help="skip the ragged-batch and serving measurements")
-    ap.add_argument("--extras", default="unfused,precision,rda_full,long_lines,ragged_batch,serving",
+    ap.add_argument("--extras", default="unfused,precision,rda_full,long_lines,any_length,ragged_batch,serving",
                     help="comma-separated extra measurements to run after the headline step")
     return ap.parse_args()
 
@@ -303,6 +303,42 @@ def long_lines_bench(sar, stream, peak, reps: int = 10) -> dict:
         out[str(n)] = {"lines": n_lines, "best": best["name"], "ms": best_ms,
                        "gb_s": gbs[best["name"]], "frac_hbm": gbs[best["name"]] / peak,
                        "all_gb_s": {k: round(v, 1) for k, v in sorted(gbs.items(), key=lambda x: -x[1])}}
+    return out
+
+
+# ---------------------------------------------------------------------------
+# line lengths that are not powers of two (zero-padded linear convolution)
+# ---------------------------------------------------------------------------
+
+def any_length_bench(sar, dev, stream, peak, reps: int = 20) -> dict:
+    """The fused range pass over about 384 MiB of lines of n samples for
+    lengths that are not powers of two (engine length L = next pow2 >=
+    2n - 1), beside the power-of-two lengths around them; GB/s over 16 B per
+    sample of n (one read and one write)."""
+    import torch
+    out = {}
+    for n in (1000, 1024, 3000, 4096, 5000, 8000, 8192):
+        n_lines = 1 << max(8, ((384 << 20) // (8 * n) - 1).bit_length())
+        data = torch.zeros((n_lines, n), dtype=torch.complex64, device=dev)
+        Hr = torch.ones(n, dtype=torch.complex64, device=dev)
+        Ha = torch.ones(n_lines, dtype=torch.complex64, device=dev)
+        plan = sar.sar_plan_create(n, n_lines, Hr, Ha)
+        L = sar.sar_plan_get_schedules(plan)[0]["n"]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        times = []
+        for i in range(reps + 3):
+            e0.record(stream)
+            sar.sar_range_compress(plan, data, stream)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= 3:
+                times.append(e0.elapsed_time(e1))
+        times.sort()
+        ms = times[len(times) // 2]
+        gbs = 16.0 * n * n_lines / (ms * 1e-3) / 1e9
+        out[str(n)] = {"engine_length": L, "lines": n_lines, "ms": ms, "gb_s": gbs, "frac_hbm": gbs / peak}
+        plan.destroy()
+        del data
     return out
 
 
@@ -586,7 +622,7 @@ def main():
 
     extras = {}
     wanted = set() if args.no_extras else {x.strip() for x in args.extras.split(",") if x.strip()}
-    unknown = wanted - {"unfused", "precision", "rda_full", "long_lines", "ragged_batch", "serving"}
+    unknown = wanted - {"unfused", "precision", "rda_full", "long_lines", "any_length", "ragged_batch", "serving"}
     if unknown:
         raise SystemExit(f"bench.py: unknown extras {sorted(unknown)}")
     if "unfused" in wanted:
@@ -597,6 +633,8 @@ def main():
         extras["rda_full"] = rda_full_bench(sar, dev, stream, work, image)
     if "long_lines" in wanted:
         extras["long_lines"] = long_lines_bench(sar, stream, peak)
+    if "any_length" in wanted:
+        extras["any_length"] = any_length_bench(sar, dev, stream, peak)
     if "ragged_batch" in wanted:
         extras["ragged_batch"] = ragged_batch_bench(sar, roofline, dev, stream, peak)
     if "serving" in wanted:
