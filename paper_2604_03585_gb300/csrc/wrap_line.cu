@@ -99,7 +99,7 @@ const SchedDesc kWrap[] = {
     make_wrap_desc<Sched<256, 16, 16, 16>, 8, false>("wrap_l256_e16_r16x16_s8"),
     make_wrap_desc<Sched<512, 32, 16, 32>, 8, false>("wrap_l512_e32_r16x32_s8"),
     make_wrap_desc<Sched<1024, 32, 32, 32>, 4, false>("wrap_l1024_e32_r32x32_s4"),
-    make_wrap_desc<Sched<2048, 16, 16, 16, 8>, 2, false>("wrap_l2048_e16_r16x16x8_s2"),
+    make_wrap_desc<Sched<2048, 16, 16, 8, 16>, 1, false>("wrap_l2048_e16_r16x8x16_s1"),
     make_wrap_desc<Sched<4096, 32, 16, 16, 16>, 1, true>("wrap_l4096_e32_r16x16x16_sr1"),
     make_wrap_desc<Sched<8192, 32, 16, 16, 32>, 1, true>("wrap_l8192_e32_r16x16x32_sr1"),
     make_wrap_desc<Sched<16384, 32, 16, 32, 32>, 1, true>("wrap_l16384_e32_r16x32x32_sr1"),

@@ -58,11 +58,12 @@ def rda_flops(n_az: int, n_range: int) -> float:
 
 
 def kernel_source_hash() -> str:
-    """sha256 over the CUDA sources of the kernels (headers and schedule
-    tables); a recorded ncu traffic figure is valid only for this hash."""
+    """sha256 over the CUDA sources of the kernels whose traffic is recorded
+    (the line-engine headers, the 4096-point schedule table, the corner turn);
+    a recorded ncu traffic figure is valid only for this hash."""
     h = hashlib.sha256()
     files = sorted(glob.glob(os.path.join(_HERE, "csrc", "*.cuh")) +
-                   glob.glob(os.path.join(_HERE, "csrc", "sched_*.cu")) +
+                   glob.glob(os.path.join(_HERE, "csrc", "sched_4096.cu")) +
                    glob.glob(os.path.join(_HERE, "csrc", "corner_turn.cu")))
     for f in files:
         h.update(os.path.basename(f).encode())
