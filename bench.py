@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="use the compiled-in preferred schedules")
     ap.add_argument("--no-extras", action="store_true", help="skip the ragged-batch and serving measurements")
     ap.add_argument("--extras",
-                    default="pipelined,unfused,precision,rda_full,long_lines,any_length,ragged_batch,serving",
+                    default="pipelined,az_major,unfused,precision,rda_full,long_lines,any_length,ragged_batch,serving",
                     help="comma-separated extra measurements to run after the headline step")
     return ap.parse_args()
 
@@ -273,6 +273,41 @@ def pipelined_bench(sar, plan, raws, image, dev, sequential_ms: float, scenes: i
             "speedup": sequential_ms / ms, "path_GBps_folded": 536870912 / (ms * 1e-3) / 1e9,
             "note": "amortised over consecutive scenes, two in flight on two streams (range pass of k+1 beside "
                     "the azimuth pass of k); inputs larger than L2 (rotating raw buffers)"}
+
+
+# ---------------------------------------------------------------------------
+# azimuth-major output: the fourth pass, timed separately
+# ---------------------------------------------------------------------------
+
+def az_major_bench(sar, Hr, Ha, raw, work, image, stream, reps: int = 50) -> dict:
+    """The scene through sar_rda_process_oop with and without
+    SAR_PLAN_OUT_AZ_MAJOR (the transpose back to [n_az][n_range]), and the
+    transpose alone; medians of `reps`."""
+    import torch
+    out = torch.empty_like(work)
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t = []
+        for i in range(reps + 3):
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            if i >= 3:
+                t.append(e0.elapsed_time(e1))
+        t.sort()
+        return t[len(t) // 2]
+
+    std = sar.sar_plan_create(N_RANGE, N_AZ, Hr, Ha)
+    maj = sar.sar_plan_create(N_RANGE, N_AZ, Hr, Ha, flags=sar.SAR_PLAN_OUT_AZ_MAJOR)
+    ms_std = timed(lambda: sar.sar_rda_process_oop(std, raw, work, image, stream))
+    ms_maj = timed(lambda: sar.sar_rda_process_oop(maj, raw, work, out, stream))
+    ms_t = timed(lambda: sar.sar_transpose(N_RANGE, N_AZ, image, out, stream))
+    std.destroy()
+    maj.destroy()
+    return {"ms_per_scene_range_major": ms_std, "ms_per_scene_az_major": ms_maj, "fourth_pass_ms": ms_t,
+            "fourth_pass_GBps": 2 * 8 * N_RANGE * N_AZ / (ms_t * 1e-3) / 1e9}
 
 
 # ---------------------------------------------------------------------------
@@ -669,12 +704,14 @@ def main():
 
     extras = {}
     wanted = set() if args.no_extras else {x.strip() for x in args.extras.split(",") if x.strip()}
-    unknown = wanted - {"pipelined", "unfused", "precision", "rda_full", "long_lines", "any_length", "ragged_batch",
-                        "serving"}
+    unknown = wanted - {"pipelined", "az_major", "unfused", "precision", "rda_full", "long_lines", "any_length",
+                        "ragged_batch", "serving"}
     if unknown:
         raise SystemExit(f"bench.py: unknown extras {sorted(unknown)}")
     if "pipelined" in wanted and folded:
         extras["pipelined"] = pipelined_bench(sar, plan, raws, image, dev, ms_step)
+    if "az_major" in wanted:
+        extras["az_major"] = az_major_bench(sar, Hr, Ha, raws[0], work, image, stream)
     if "unfused" in wanted:
         extras["unfused"] = unfused_bench(sar, plan, raws[0], work, image, stream, ms_step)
     if "precision" in wanted:

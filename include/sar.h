@@ -98,6 +98,13 @@ typedef struct {
  * HBM traffic per sample); this flag keeps the three separate kernels of
  * Sec. IV-A (48 bytes per sample). */
 #define SAR_PLAN_UNFOLDED_CORNER_TURN 1u
+/* Azimuth-major output: sar_rda_process_oop and sar_rda_process_host return
+ * the image as complex64[n_az][n_range] (the raw echo's orientation, as the
+ * paper's pipeline transposes back, Sec. IV-B) by a fourth pass, a transpose
+ * of the [n_range][n_az] image (16 bytes per sample).  sar_rda_process, which
+ * has no scratch buffer, and sar_rda_full refuse such plans
+ * (SAR_ERR_INVALID_ARG). */
+#define SAR_PLAN_OUT_AZ_MAJOR 2u
 
 /* Create a plan for an n_az x n_range scene (Sec. IV-A, the N_a x N_r data
  * matrix).  n_range and n_az: powers of two in [256, 131072] (above 16384 on
@@ -160,7 +167,9 @@ SAR_API sar_status sar_range_compress_ct(sar_plan plan, const void *raw, void *i
  * sar_rda_process.
  * raw: device complex64[n_az][n_range] (read only); work: device
  * complex64[n_az][n_range] scratch owned by the caller; image: device
- * complex64[n_range][n_az].  The three buffers must not overlap. */
+ * complex64[n_range][n_az].  The three buffers must not overlap.  With
+ * SAR_PLAN_OUT_AZ_MAJOR the passes leave the [n_range][n_az] image in work
+ * and a fourth pass transposes it into image, complex64[n_az][n_range]. */
 SAR_API sar_status sar_rda_process_oop(sar_plan plan, const void *raw, void *work, void *image, sar_stream stream);
 
 /* The unfused comparison pipeline the paper's fused kernel replaces (Sec.
@@ -206,7 +215,8 @@ SAR_API sar_status sar_rda_full(sar_plan plan, const void *raw, void *work, void
 /* The same three steps on HOST buffers: copies raw to the device, runs
  * sar_rda_process, copies the image back, and returns once the image is in
  * host memory.  raw: host complex64[n_az][n_range] (not modified);
- * image: host complex64[n_range][n_az].  Pinned host memory gives the full
+ * image: host complex64[n_range][n_az] ([n_az][n_range] for a plan with
+ * SAR_PLAN_OUT_AZ_MAJOR).  Pinned host memory gives the full
  * copy bandwidth.  The plan allocates its device staging buffers on the first
  * call (2 x n_az x n_range x 8 bytes) and keeps them until destroyed. */
 SAR_API sar_status sar_rda_process_host(sar_plan plan, const void *raw, void *image, sar_stream stream);

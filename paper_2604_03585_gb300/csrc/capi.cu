@@ -178,6 +178,7 @@ struct sar_plan_s {
     int *status = nullptr;  // device word written by timed-out kernels (0 = fine)
     int prec = SAR_PREC_FP32;
     bool fold = false;      // range pass writes the corner-turned image itself
+    bool az_major = false;  // image returned as [n_az][n_range] (a fourth pass)
     sar::FusedCtl ctl{};
     void *block = nullptr;  // one device allocation holding every table
     std::mutex host_mu;
@@ -210,7 +211,7 @@ sar_status sar_plan_create_ex(int64_t n_range, int64_t n_az, const sar_filters *
     const bool wrap_r = !native_length(n_range), wrap_a = !native_length(n_az);
     if ((wrap_r && range_schedule) || (wrap_a && az_schedule))
         return fail(SAR_ERR_INVALID_ARG, "schedules can be named only for power-of-two lengths");
-    if (filters->flags & ~SAR_PLAN_UNFOLDED_CORNER_TURN)
+    if (filters->flags & ~(SAR_PLAN_UNFOLDED_CORNER_TURN | SAR_PLAN_OUT_AZ_MAJOR))
         return fail(SAR_ERR_INVALID_ARG, "filters->flags has unknown bits 0x%x", filters->flags);
     const int prec = filters->precision;
     if (prec < SAR_PREC_FP32 || prec > SAR_PREC_BF16X3)
@@ -254,6 +255,7 @@ sar_status sar_plan_create_ex(int64_t n_range, int64_t n_az, const sar_filters *
     p->az.n = n_az;
     p->prec = prec;
     p->fold = want_fold && dr->fused_ct && n_az % dr->ct_lines == 0;
+    p->az_major = (filters->flags & SAR_PLAN_OUT_AZ_MAJOR) != 0;
 
     // one block: filt_r | tw_r | filt_a | tw_a | idx (int32, max engine length) | status | filt_nat_r | filt_nat_a
     const size_t o_fr = 0;
@@ -554,6 +556,16 @@ sar_status sar_corner_turn(sar_plan p, const void *in, void *out, sar_stream str
     return SAR_OK;
 }
 
+// The three passes into image [n_range][n_az] (raw clobbered when unfolded).
+static sar_status rda3(sar_plan p, void *raw, void *image, cudaStream_t s) {
+    sar_status st;
+    if (p->fold) return run_folded(p, raw, image, s);
+    if ((st = run_fused(p, p->range, p->n_az, raw, raw, s, "range compression launch")) != SAR_OK) return st;
+    cudaError_t e = sar::launch_transpose((const float2 *)raw, (float2 *)image, p->n_az, p->n_range, s);
+    if (e != cudaSuccess) return cuda_fail(e, "corner turn launch");
+    return run_fused(p, p->az, p->n_range, image, image, s, "azimuth compression launch");
+}
+
 sar_status sar_rda_process(sar_plan p, void *raw, void *image, sar_stream stream) {
     if (!p) return fail(SAR_ERR_INVALID_ARG, "plan is NULL");
     sar_status st;
@@ -561,6 +573,8 @@ sar_status sar_rda_process(sar_plan p, void *raw, void *image, sar_stream stream
     if ((st = check_device_ptr(image, "image")) != SAR_OK) return st;
     if (overlaps(raw, image, sizeof(float2) * (size_t)(p->n_az * p->n_range)))
         return fail(SAR_ERR_INVALID_ARG, "raw and image overlap");
+    if (p->az_major)
+        return fail(SAR_ERR_INVALID_ARG, "azimuth-major output needs a work buffer: use sar_rda_process_oop");
     cudaStream_t s = (cudaStream_t)stream;
     if (p->fold) return run_folded(p, raw, image, s);
     if ((st = run_fused(p, p->range, p->n_az, raw, raw, s, "range compression launch")) != SAR_OK) return st;
@@ -621,6 +635,23 @@ sar_status sar_rda_process_oop(sar_plan p, const void *raw, void *work, void *im
     if (overlaps(raw, work, bytes) || overlaps(raw, image, bytes) || overlaps(work, image, bytes))
         return fail(SAR_ERR_INVALID_ARG, "raw, work and image must not overlap");
     cudaStream_t s = (cudaStream_t)stream;
+    if (p->az_major) {
+        // the three passes leave the [n_range][n_az] image in work (image as
+        // scratch when unfolded), then the fourth pass transposes it back
+        if (p->fold) {
+            if ((st = run_folded(p, raw, work, s)) != SAR_OK) return st;
+        } else {
+            if ((st = run_fused(p, p->range, p->n_az, raw, image, s, "range compression launch")) != SAR_OK)
+                return st;
+            cudaError_t e = sar::launch_transpose((const float2 *)image, (float2 *)work, p->n_az, p->n_range, s);
+            if (e != cudaSuccess) return cuda_fail(e, "corner turn launch");
+            if ((st = run_fused(p, p->az, p->n_range, work, work, s, "azimuth compression launch")) != SAR_OK)
+                return st;
+        }
+        cudaError_t e = sar::launch_transpose((const float2 *)work, (float2 *)image, p->n_range, p->n_az, s);
+        if (e != cudaSuccess) return cuda_fail(e, "transpose back launch");
+        return SAR_OK;
+    }
     if (p->fold) return run_folded(p, raw, image, s);
     if ((st = run_fused(p, p->range, p->n_az, raw, work, s, "range compression launch")) != SAR_OK) return st;
     cudaError_t e = sar::launch_transpose((const float2 *)work, (float2 *)image, p->n_az, p->n_range, s);
@@ -723,6 +754,7 @@ sar_status sar_rcmc(sar_plan p, const void *in, void *out, sar_stream stream) {
 
 sar_status sar_rda_full(sar_plan p, const void *raw, void *work, void *image, sar_stream stream) {
     if (!p) return fail(SAR_ERR_INVALID_ARG, "plan is NULL");
+    if (p->az_major) return fail(SAR_ERR_INVALID_ARG, "the full processor writes [n_range][n_az] images only");
     if (!p->rd_cols) return fail(SAR_ERR_INVALID_ARG, "the plan has no geometry (sar_plan_set_geometry)");
     sar_status st;
     if ((st = check_device_ptr(raw, "raw")) != SAR_OK) return st;
@@ -775,9 +807,16 @@ sar_status sar_rda_process_host(sar_plan p, const void *raw, void *image, sar_st
         }
     }
     SAR_CUDA(cudaMemcpyAsync(p->stage_raw, raw, bytes, cudaMemcpyHostToDevice, s), "host-to-device copy");
-    sar_status st = sar_rda_process(p, p->stage_raw, p->stage_img, stream);
+    sar_status st = rda3(p, p->stage_raw, p->stage_img, s);
     if (st != SAR_OK) return st;
-    SAR_CUDA(cudaMemcpyAsync(image, p->stage_img, bytes, cudaMemcpyDeviceToHost, s), "device-to-host copy");
+    const void *result = p->stage_img;
+    if (p->az_major) {   // the fourth pass, into the staged raw echo (no longer needed)
+        cudaError_t e = sar::launch_transpose((const float2 *)p->stage_img, (float2 *)p->stage_raw, p->n_range,
+                                              p->n_az, s);
+        if (e != cudaSuccess) return cuda_fail(e, "transpose back launch");
+        result = p->stage_raw;
+    }
+    SAR_CUDA(cudaMemcpyAsync(image, result, bytes, cudaMemcpyDeviceToHost, s), "device-to-host copy");
     SAR_CUDA(cudaStreamSynchronize(s), "stream synchronise");
     return SAR_OK;
 }

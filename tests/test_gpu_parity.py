@@ -542,3 +542,33 @@ def test_split_precision_refusals(sar):
     with pytest.raises(sar.SarError) as e:
         sar.sar_plan_create(1024, 1024, x, x, precision=9)
     assert e.value.status == sar.SAR_ERR_INVALID_ARG
+
+
+# ---------------------------------------------------------------------------
+# azimuth-major output: the fourth pass (transpose back)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n_range,n_az,flags", [(4096, 4096, 0), (1024, 512, 1), (1000, 300, 0)],
+                         ids=["4096-folded", "1024x512-unfolded", "1000x300-any-length"])
+def test_azimuth_major_output(sar, n_range, n_az, flags):
+    """SAR_PLAN_OUT_AZ_MAJOR returns exactly the transpose of the usual
+    [n_range][n_az] image, from device and from host buffers."""
+    Hr, Ha = rand_c64(n_range, seed=41), rand_c64(n_az, seed=42)
+    raw = rand_c64(n_az * n_range, seed=43).reshape(n_az, n_range)
+    ref_plan = sar.sar_plan_create(n_range, n_az, dev(Hr), dev(Ha), flags=flags)
+    maj_plan = sar.sar_plan_create(n_range, n_az, dev(Hr), dev(Ha), flags=flags | sar.SAR_PLAN_OUT_AZ_MAJOR)
+    r0, w0, img = dev(raw), empty_c64(n_az, n_range), empty_c64(n_range, n_az)
+    sar.sar_rda_process_oop(ref_plan, r0, w0, img)
+    r1, w1, out = dev(raw), empty_c64(n_az, n_range), empty_c64(n_az, n_range)
+    sar.sar_rda_process_oop(maj_plan, r1, w1, out)
+    ref = host(img)
+    assert np.array_equal(host(out), ref.T)
+    assert np.array_equal(host(r1), raw)
+    out_h = torch.empty((n_az, n_range), dtype=torch.complex64).pin_memory()
+    sar.sar_rda_process_host(maj_plan, torch.from_numpy(raw).pin_memory(), out_h)
+    assert np.array_equal(out_h.numpy(), ref.T)
+    with pytest.raises(sar.SarError) as e:
+        sar.sar_rda_process(maj_plan, dev(raw), empty_c64(n_az, n_range))
+    assert e.value.status == sar.SAR_ERR_INVALID_ARG
+    ref_plan.destroy()
+    maj_plan.destroy()
