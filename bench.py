@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="use the compiled-in preferred schedules")
     ap.add_argument("--no-extras", action="store_true", help="skip the ragged-batch and serving measurements")
     ap.add_argument("--extras",
-                    default="pipelined,az_major,unfused,precision,rda_full,long_lines,any_length,ragged_batch,serving",
+                    default="passes,scene_256,pipelined,az_major,unfused,precision,rda_full,long_lines,any_length,"
+                            "ragged_batch,serving",
                     help="comma-separated extra measurements to run after the headline step")
     return ap.parse_args()
 
@@ -227,6 +228,103 @@ def reference_arm(args, rank, world):
            "cpu_baseline": {"value": v, "unit": "ms", "cores": nth, "kind": "oracle", "sample": sample},
            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the 4096^2 scene's three passes timed separately (corner turn not folded)
+# ---------------------------------------------------------------------------
+
+def _median_ms(stream, fn, reps: int = 20, warm: int = 3) -> float:
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t = []
+    for i in range(reps + warm):
+        e0.record(stream)
+        fn(i)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= warm:
+            t.append(e0.elapsed_time(e1))
+    t.sort()
+    return t[len(t) // 2]
+
+
+def passes_bench(sar, Hr, Ha, raws, work, image, stream) -> dict:
+    """Range pass, corner turn and azimuth pass of the 4096^2 scene as three
+    separate kernels (an unfolded plan), each the median of 20 launches over
+    rotating inputs larger than L2; GB/s over 16 B per sample each."""
+    plan = sar.sar_plan_create(N_RANGE, N_AZ, Hr, Ha, flags=sar.SAR_PLAN_UNFOLDED_CORNER_TURN)
+    ms_r = _median_ms(stream, lambda i: sar.sar_range_compress_oop(plan, raws[i % len(raws)], work, stream))
+    ms_c = _median_ms(stream, lambda i: sar.sar_corner_turn(plan, raws[i % len(raws)], image, stream))
+    ms_a = _median_ms(stream, lambda i: sar.sar_azimuth_compress(plan, image, stream))
+    plan.destroy()
+    b = 16.0 * N_RANGE * N_AZ
+    return {"range_pass_ms": ms_r, "corner_turn_ms": ms_c, "azimuth_pass_ms": ms_a,
+            "range_pass_GBps": b / (ms_r * 1e-3) / 1e9, "corner_turn_GBps": b / (ms_c * 1e-3) / 1e9,
+            "azimuth_pass_GBps": b / (ms_a * 1e-3) / 1e9, "sum_ms": ms_r + ms_c + ms_a}
+
+
+# ---------------------------------------------------------------------------
+# the 256 x 256 scene: per pass, end to end as one CUDA-graph launch, oracle
+# ---------------------------------------------------------------------------
+
+def scene_256_bench(sar, dev, stream, host_threads: int, graph_reps: int = 1000) -> dict:
+    import numpy as np
+    import torch
+    import sarsim
+    spec = sarsim.scene_256()
+    n = 256
+    raw_np = sarsim.echo(spec)
+    raw = torch.from_numpy(raw_np).to(dev)
+    Hr = torch.empty(n, dtype=torch.complex64, device=dev)
+    Ha = torch.empty(n, dtype=torch.complex64, device=dev)
+    sar.sar_make_lfm_spectrum(n, *spec.range_chirp, Hr, stream)
+    sar.sar_make_lfm_spectrum(n, *spec.az_chirp, Ha, stream)
+    stream.synchronize()
+    work, image = torch.empty_like(raw), torch.empty_like(raw)
+    plan = sar.sar_plan_create(n, n, Hr, Ha)
+    flat = sar.sar_plan_create(n, n, Hr, Ha, flags=sar.SAR_PLAN_UNFOLDED_CORNER_TURN)
+    out = {"folded": sar.sar_plan_folds_corner_turn(plan)}
+    us = lambda fn: 1e3 * _median_ms(stream, fn)
+    if out["folded"]:
+        out["range_pass_with_corner_turn_us"] = us(lambda i: sar.sar_range_compress_ct(plan, raw, image, stream))
+    out["range_pass_us"] = us(lambda i: sar.sar_range_compress_oop(flat, raw, work, stream))
+    out["corner_turn_us"] = us(lambda i: sar.sar_corner_turn(flat, work, image, stream))
+    out["azimuth_pass_us"] = us(lambda i: sar.sar_azimuth_compress(flat, image, stream))
+    # end to end: the whole scene as one CUDA-graph launch
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        sar.sar_rda_process_oop(plan, raw, work, image, stream)      # warm (tables, attributes)
+        stream.synchronize()
+        with torch.cuda.graph(g, stream=stream, capture_error_mode="relaxed"):
+            sar.sar_rda_process_oop(plan, raw, work, image, stream)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(10):
+        g.replay()
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(graph_reps):
+            g.replay()
+    e1.record(stream)
+    e1.synchronize()
+    out["graph_us_per_scene"] = 1e3 * e0.elapsed_time(e1) / graph_reps
+    plan.destroy()
+    flat.destroy()
+    if host_threads:
+        import oracle
+        o = oracle.default()
+        Hr64 = o.matched_filter(n, sarsim.lfm_chirp(*spec.range_chirp))
+        Ha64 = o.matched_filter(n, sarsim.lfm_chirp(*spec.az_chirp))
+        for label, nth in (("oracle_ms_1_thread", 1), ("oracle_ms_all_threads", host_threads)):
+            t = []
+            for _ in range(5):
+                t0 = time.perf_counter()
+                o.rda(raw_np, Hr64, Ha64, nthreads=nth)
+                t.append((time.perf_counter() - t0) * 1e3)
+            out[label] = sorted(t)[2]
+        out["oracle_threads"] = host_threads
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -698,16 +796,23 @@ def main():
         Ha64 = o.matched_filter(N_AZ, sarsim.lfm_chirp(*spec.az_chirp))
         lines = 512
         v = oracle_scene_ms(raw_np, Hr64, Ha64, lines, nth)
+        v1 = oracle_scene_ms(raw_np, Hr64, Ha64, 64, 1)
         cpu = {"value": v, "unit": "ms", "cores": nth, "kind": "oracle",
                "sample": f"{lines} range + {lines} azimuth lines of the 4096x4096 scene (FP64 C oracle, "
-                         f"{nth} threads), scaled x{N_AZ // lines} to one scene"}
+                         f"{nth} threads), scaled x{N_AZ // lines} to one scene",
+               "single_thread_ms": v1, "single_thread_sample": "64 + 64 lines, one thread, scaled x64",
+               "nproc": os.cpu_count()}
 
     extras = {}
     wanted = set() if args.no_extras else {x.strip() for x in args.extras.split(",") if x.strip()}
-    unknown = wanted - {"pipelined", "az_major", "unfused", "precision", "rda_full", "long_lines", "any_length",
-                        "ragged_batch", "serving"}
+    unknown = wanted - {"passes", "scene_256", "pipelined", "az_major", "unfused", "precision", "rda_full",
+                        "long_lines", "any_length", "ragged_batch", "serving"}
     if unknown:
         raise SystemExit(f"bench.py: unknown extras {sorted(unknown)}")
+    if "passes" in wanted:
+        extras["passes"] = passes_bench(sar, Hr, Ha, raws, work, image, stream)
+    if "scene_256" in wanted:
+        extras["scene_256"] = scene_256_bench(sar, dev, stream, cpu_threads() if rank == 0 else 0)
     if "pipelined" in wanted and folded:
         extras["pipelined"] = pipelined_bench(sar, plan, raws, image, dev, ms_step)
     if "az_major" in wanted:
