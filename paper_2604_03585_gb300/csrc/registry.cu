@@ -12,7 +12,9 @@ struct All {
     const SchedDesc *p[96];
     int n = 0;
     All() {
-        const SchedDesc *(*tables[])(int *) = {schedules_small, schedules_4096, schedules_large, schedules_cluster};
+        const SchedDesc *(*tables[])(int *) = {schedules_small,      schedules_2048,      schedules_4096,
+                                                  schedules_4096_plain, schedules_4096_more, schedules_8192,
+                                                  schedules_16384,      schedules_cluster};
         for (auto f : tables) {
             int c = 0;
             const SchedDesc *t = f(&c);

@@ -53,9 +53,13 @@ struct SchedDesc {
 };
 
 // All compiled schedules (one table per translation unit).
-const SchedDesc *schedules_small(int *count);   // N = 256 .. 2048
-const SchedDesc *schedules_4096(int *count);
-const SchedDesc *schedules_large(int *count);   // N = 8192, 16384
+const SchedDesc *schedules_small(int *count);   // N = 256 .. 1024
+const SchedDesc *schedules_2048(int *count);
+const SchedDesc *schedules_4096(int *count);        // first: the default of 4096
+const SchedDesc *schedules_4096_plain(int *count);
+const SchedDesc *schedules_4096_more(int *count);
+const SchedDesc *schedules_8192(int *count);
+const SchedDesc *schedules_16384(int *count);
 const SchedDesc *schedules_cluster(int *count); // N = 32768 ... 131072, one line per cluster
 
 // The preferred schedule for length n, or nullptr.
