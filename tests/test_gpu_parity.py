@@ -572,3 +572,28 @@ def test_azimuth_major_output(sar, n_range, n_az, flags):
     assert e.value.status == sar.SAR_ERR_INVALID_ARG
     ref_plan.destroy()
     maj_plan.destroy()
+
+
+# ---------------------------------------------------------------------------
+# twiddle tables against their FP64 closed form
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", NS + [32768, 65536, 131072])
+def test_fft_of_impulse_is_the_closed_form_root(sar, n):
+    """The FFT of the impulse at index 1 is exp(-2 pi i k / N) and of the one at
+    N - 1 is exp(+2 pi i k / N): every output is a product of twiddle-table
+    entries (FP64 phases rounded once to FP32, then the roots table of the
+    cluster lengths), so each must equal the closed form to a few FP32 ulps;
+    one wrong entry would show as an O(1) error."""
+    x = np.zeros((2, n), np.complex64)
+    x[0, 1] = 1.0
+    x[1, n - 1] = 1.0
+    xd = dev(x)
+    out = torch.empty_like(xd)
+    sar.sar_fft_lines(n, 2, xd, out)
+    got = host(out).astype(np.complex128)
+    k = np.arange(n)
+    ref = np.stack([np.exp(-2j * np.pi * k / n), np.exp(2j * np.pi * k / n)])
+    err = np.max(np.abs(got - ref))
+    print(f"\nTWIDDLE n={n}: max |X - exp(-+2 pi i k/N)| = {err:.2e} ({err / 2 ** -24:.1f} x 2^-24)")
+    assert err < 16 * 2 ** -24
