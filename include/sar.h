@@ -218,7 +218,12 @@ SAR_API sar_status sar_rda_full(sar_plan plan, const void *raw, void *work, void
  * image: host complex64[n_range][n_az] ([n_az][n_range] for a plan with
  * SAR_PLAN_OUT_AZ_MAJOR).  Pinned host memory gives the full
  * copy bandwidth.  The plan allocates its device staging buffers on the first
- * call (2 x n_az x n_range x 8 bytes) and keeps them until destroyed. */
+ * call (2 x n_az x n_range x 8 bytes) and keeps them until destroyed.  On a
+ * plan that folds the corner turn the call is a pipeline on two internal
+ * streams: the echo arrives in 8 blocks of azimuth lines and each block's
+ * range pass starts as soon as it has landed; the azimuth pass runs in 8
+ * blocks of range bins, each copied back while the next is computed.  One
+ * host-buffer call per plan runs at a time. */
 SAR_API sar_status sar_rda_process_host(sar_plan plan, const void *raw, void *image, sar_stream stream);
 
 /* Matched-filter helper (Sec. II-B step 3, Sec. V-A's chirp signal model):

@@ -183,6 +183,11 @@ struct sar_plan_s {
     void *block = nullptr;  // one device allocation holding every table
     std::mutex host_mu;
     void *stage_raw = nullptr, *stage_img = nullptr;  // lazily, for the host-buffer entry point
+    // lazily, for the chunked host-buffer pipeline: a copy and a compute stream,
+    // one event per chunk and direction, and start / end events
+    static constexpr int kHostChunks = 8;
+    cudaStream_t host_copy = nullptr, host_compute = nullptr;
+    cudaEvent_t host_ev[2 * kHostChunks + 2] = {};
     // full Range-Doppler processing (sar_plan_set_geometry)
     void *rd_cols = nullptr;
     double kappa = 0, vs = 0, r_near = 0;
@@ -497,6 +502,10 @@ sar_status sar_plan_destroy(sar_plan p) {
     if (p->stage_raw) cudaFree(p->stage_raw);
     if (p->stage_img) cudaFree(p->stage_img);
     if (p->rd_cols) cudaFree(p->rd_cols);
+    if (p->host_copy) cudaStreamDestroy(p->host_copy);
+    if (p->host_compute) cudaStreamDestroy(p->host_compute);
+    for (cudaEvent_t e : p->host_ev)
+        if (e) cudaEventDestroy(e);
     delete p;
     return SAR_OK;
 }
@@ -790,22 +799,74 @@ sar_status sar_rda_full(sar_plan p, const void *raw, void *work, void *image, sa
     return SAR_OK;
 }
 
+// The host-buffer path of a folded plan as a pipeline: the echo arrives in
+// kHostChunks blocks of azimuth lines on a copy stream, and each block's
+// range pass (with the folded corner turn, into its columns of the image)
+// starts on a compute stream as soon as the block has landed; the azimuth
+// pass then runs over kHostChunks blocks of range bins, each copied back while
+// the next is computed.  The copies, one direction at a time, set the pace;
+// the compute hides behind them.  Called with p->host_mu held and the staging
+// buffers allocated.
+static sar_status host_pipeline(sar_plan p, const void *raw, void *image, cudaStream_t s) {
+    constexpr int K = sar_plan_s::kHostChunks;
+    const SchedDesc &dr = *p->range.sched;
+    const int64_t A = p->n_az / K, B = p->n_range / K;
+    if (!p->host_copy) {
+        SAR_CUDA(cudaStreamCreateWithFlags(&p->host_copy, cudaStreamNonBlocking), "cudaStreamCreate");
+        SAR_CUDA(cudaStreamCreateWithFlags(&p->host_compute, cudaStreamNonBlocking), "cudaStreamCreate");
+        for (cudaEvent_t &e : p->host_ev) SAR_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+    }
+    cudaStream_t sc = p->host_copy, sk = p->host_compute;
+    cudaEvent_t *ev_in = p->host_ev, *ev_out = p->host_ev + K, ev_start = p->host_ev[2 * K],
+                ev_end = p->host_ev[2 * K + 1];
+    float2 *sraw = (float2 *)p->stage_raw, *simg = (float2 *)p->stage_img;
+    const size_t row_r = sizeof(float2) * (size_t)p->n_range, row_a = sizeof(float2) * (size_t)p->n_az;
+    SAR_CUDA(cudaEventRecord(ev_start, s), "cudaEventRecord");
+    SAR_CUDA(cudaStreamWaitEvent(sc, ev_start, 0), "cudaStreamWaitEvent");
+    SAR_CUDA(cudaStreamWaitEvent(sk, ev_start, 0), "cudaStreamWaitEvent");
+    for (int k = 0; k < K; ++k) {
+        SAR_CUDA(cudaMemcpyAsync(sraw + k * A * p->n_range, (const char *)raw + k * A * row_r, A * row_r,
+                                 cudaMemcpyHostToDevice, sc),
+                 "host-to-device copy");
+        SAR_CUDA(cudaEventRecord(ev_in[k], sc), "cudaEventRecord");
+        SAR_CUDA(cudaStreamWaitEvent(sk, ev_in[k], 0), "cudaStreamWaitEvent");
+        cudaError_t e = dr.fused_ct(sraw + k * A * p->n_range, simg + k * A, A, p->n_range, p->n_az, p->range.filt,
+                                    p->range.tw, sk);
+        if (e != cudaSuccess) return cuda_fail(e, "range compression + corner turn launch");
+    }
+    for (int j = 0; j < K; ++j) {
+        float2 *rows = simg + j * B * p->n_az;
+        sar_status st = run_fused(p, p->az, B, rows, rows, sk, "azimuth compression launch");
+        if (st != SAR_OK) return st;
+        SAR_CUDA(cudaEventRecord(ev_out[j], sk), "cudaEventRecord");
+        SAR_CUDA(cudaStreamWaitEvent(sc, ev_out[j], 0), "cudaStreamWaitEvent");
+        SAR_CUDA(cudaMemcpyAsync((char *)image + j * B * row_a, rows, B * row_a, cudaMemcpyDeviceToHost, sc),
+                 "device-to-host copy");
+    }
+    SAR_CUDA(cudaEventRecord(ev_end, sc), "cudaEventRecord");
+    SAR_CUDA(cudaStreamWaitEvent(s, ev_end, 0), "cudaStreamWaitEvent");
+    SAR_CUDA(cudaStreamSynchronize(s), "stream synchronise");
+    return SAR_OK;
+}
+
 sar_status sar_rda_process_host(sar_plan p, const void *raw, void *image, sar_stream stream) {
     if (!p) return fail(SAR_ERR_INVALID_ARG, "plan is NULL");
     if (!raw || !image) return fail(SAR_ERR_INVALID_ARG, "raw or image is NULL");
     const size_t bytes = sizeof(float2) * (size_t)(p->n_az * p->n_range);
     cudaStream_t s = (cudaStream_t)stream;
-    {
-        std::lock_guard<std::mutex> lk(p->host_mu);
-        if (!p->stage_raw) {
-            if (cudaMalloc(&p->stage_raw, bytes) != cudaSuccess || cudaMalloc(&p->stage_img, bytes) != cudaSuccess) {
-                cudaGetLastError();
-                if (p->stage_raw) cudaFree(p->stage_raw);
-                p->stage_raw = p->stage_img = nullptr;
-                return fail(SAR_ERR_OUT_OF_MEMORY, "staging buffers (2 x %zu bytes)", bytes);
-            }
+    std::lock_guard<std::mutex> lk(p->host_mu);   // one host-buffer call per plan at a time
+    if (!p->stage_raw) {
+        if (cudaMalloc(&p->stage_raw, bytes) != cudaSuccess || cudaMalloc(&p->stage_img, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            if (p->stage_raw) cudaFree(p->stage_raw);
+            p->stage_raw = p->stage_img = nullptr;
+            return fail(SAR_ERR_OUT_OF_MEMORY, "staging buffers (2 x %zu bytes)", bytes);
         }
     }
+    constexpr int K = sar_plan_s::kHostChunks;
+    const SchedDesc &dr = *p->range.sched;
+    if (p->fold && !p->az_major && p->n_az % (K * dr.ct_lines) == 0 && p->n_range % K == 0)
+        return host_pipeline(p, raw, image, s);
     SAR_CUDA(cudaMemcpyAsync(p->stage_raw, raw, bytes, cudaMemcpyHostToDevice, s), "host-to-device copy");
     sar_status st = rda3(p, p->stage_raw, p->stage_img, s);
     if (st != SAR_OK) return st;
