@@ -28,8 +28,10 @@
  *     device surfaces on a later call or on sar_sync().  sar_last_error()
  *     gives a message for the calling thread's last failure.
  *   - No C++ exception crosses this interface.
- *   - Plans take any line length in [2, 8192] (see sar_plan_create); the
- *     other entry points take powers of two from 256 to 131072.  Lines up to
+ *   - Plans, sar_fft_lines and sar_make_lfm_spectrum take any line length in
+ *     [2, 8192] besides the powers of two from 256 to 131072 (see
+ *     sar_plan_create, sar_fft_lines); the other entry points take those
+ *     powers of two.  Lines up to
  *     16384 samples run one line per thread block; longer lines run one line
  *     per thread-block cluster of 2 to 16 blocks exchanging it through
  *     distributed shared memory (sar_range_compress, sar_azimuth_compress,
@@ -232,7 +234,8 @@ SAR_API sar_status sar_rda_process_host(sar_plan plan, const void *raw, void *im
  * product tbp, c(m) = exp(i pi (tbp/n_chirp^2) m^2), m = -n_chirp/2 ...
  * n_chirp/2 - 1, centred on index 0 of the length-n line (wrapping).  The
  * chirp phase is evaluated in FP64 on the device and rounded to FP32; the
- * transform is this library's FP32 FFT.  n: power of two in [256, 131072];
+ * transform is this library's FP32 FFT.  n: power of two in [256, 131072] or
+ * any length in [2, 8192];
  * 1 <= n_chirp <= n; tbp > 0. */
 SAR_API sar_status sar_make_lfm_spectrum(int64_t n, int64_t n_chirp, double tbp, void *out, sar_stream stream);
 
@@ -254,7 +257,13 @@ SAR_API sar_status sar_simulate_echo(int64_t n_az, int64_t n_range, const int64_
 /* Unnormalised DFT of n_lines lines of length n (natural order in and out):
  * out[l][k] = sum_j in[l][j] exp(-+2 pi i j k / n), '+' when inverse != 0
  * (computed as conj(FFT(conj x)), Sec. II-C).  in and out: device
- * complex64[n_lines][n]; in place allowed.  n: power of two in [256, 131072].
+ * complex64[n_lines][n]; in place allowed.  n: power of two in [256, 131072],
+ * or any other length in [2, 8192]: then the DFT by Bluestein's identity
+ * jk = (j^2 + k^2 - (k-j)^2)/2, a chirp multiply (c_m = exp(-i pi m^2 / n),
+ * phases reduced exactly mod 2n in FP64), a linear convolution with conj(c)
+ * through the power-of-two engine at L >= 2n - 1 (filter designed in FP64 on
+ * the first call per length and cached, which allocates) and a chirp multiply
+ * of the output, in one kernel.
  * Exposes the line FFT engine on its own (tests, filter design). */
 SAR_API sar_status sar_fft_lines(int64_t n, int64_t n_lines, const void *in, void *out, int inverse, sar_stream stream);
 

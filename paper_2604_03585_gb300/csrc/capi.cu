@@ -139,6 +139,67 @@ sar_status cached_twiddles(const SchedDesc *d, float2 **out) {
     return SAR_OK;
 }
 
+// Per-device cache of the tables of the DFT of lengths that are not powers of
+// two (Bluestein): the engine schedule of length L, its twiddles, the filter
+// FFT_L(conj chirp) / L in the engine's register order, and the chirp.
+struct BluesteinCache {
+    struct Entry {
+        int n;
+        const SchedDesc *d;
+        float2 *tw, *filt, *chirp;
+    };
+    std::mutex mu;
+    std::vector<Entry> tables[64];
+};
+BluesteinCache g_bs;
+
+sar_status cached_bluestein(int n, BluesteinCache::Entry *out) {
+    int dev = 0;
+    SAR_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(SAR_ERR_UNSUPPORTED, "device index %d", dev);
+    std::lock_guard<std::mutex> lk(g_bs.mu);
+    for (auto &en : g_bs.tables[dev])
+        if (en.n == n) {
+            *out = en;
+            return SAR_OK;
+        }
+    const SchedDesc *d = sar::wrap_schedule((int)wrap_length(n));
+    if (!d) return fail(SAR_ERR_UNSUPPORTED, "no engine for length %d", n);
+    const int L = d->n;
+    const size_t o_f = align_up(sizeof(float2) * (size_t)d->tw_elems);
+    const size_t o_c = o_f + align_up(sizeof(float2) * (size_t)L);
+    const size_t total = o_c + align_up(sizeof(float2) * (size_t)n);
+    const size_t o_g = align_up(sar::bluestein_scratch_bytes(L));
+    const size_t o_i = o_g + align_up(sizeof(float2) * (size_t)L);
+    const size_t scratch_bytes = o_i + sizeof(int32_t) * (size_t)L;
+    char *block = nullptr, *scratch = nullptr;
+    if (cudaMalloc(&block, total) != cudaSuccess || cudaMalloc(&scratch, scratch_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(block);
+        return fail(SAR_ERR_OUT_OF_MEMORY, "tables of the length-%d DFT", n);
+    }
+    BluesteinCache::Entry en{n, d, (float2 *)block, (float2 *)(block + o_f), (float2 *)(block + o_c)};
+    std::vector<int32_t> idx((size_t)L);
+    sar::filter_slot_to_k(*d, idx.data());
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = sar::build_twiddles(*d, en.tw, s);
+    if (e == cudaSuccess) e = sar::build_bluestein_tables(n, L, en.chirp, (float2 *)(scratch + o_g), scratch, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(scratch + o_i, idx.data(), sizeof(int32_t) * (size_t)L, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = sar::build_filter(*d, (const float2 *)(scratch + o_g), en.filt, (int32_t *)(scratch + o_i), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (s) cudaStreamDestroy(s);
+    cudaFree(scratch);
+    if (e != cudaSuccess) {
+        cudaFree(block);
+        return cuda_fail(e, "tables of a DFT length that is not a power of two");
+    }
+    g_bs.tables[dev].push_back(en);
+    *out = en;
+    return SAR_OK;
+}
+
 bool fault_inject_alloc() {
     const char *v = getenv("SAR_FAULT_INJECT_ALLOC");
     return v && v[0] == '1';
@@ -884,6 +945,21 @@ sar_status sar_rda_process_host(sar_plan p, const void *raw, void *image, sar_st
 
 sar_status sar_fft_lines(int64_t n, int64_t n_lines, const void *in, void *out, int inverse, sar_stream stream) {
     sar_status st;
+    if (!native_length(n) && n >= 2 && n <= 8192) {
+        // a length that is not a power of two: Bluestein on the length-L engine
+        if (n_lines < 0) return fail(SAR_ERR_INVALID_ARG, "n_lines < 0");
+        if (n_lines == 0) return SAR_OK;
+        if ((st = check_device_ptr(in, "in")) != SAR_OK) return st;
+        if ((st = check_device_ptr(out, "out")) != SAR_OK) return st;
+        if (in != out && overlaps(in, out, sizeof(float2) * (size_t)(n * n_lines)))
+            return fail(SAR_ERR_INVALID_ARG, "in and out partially overlap");
+        BluesteinCache::Entry en;
+        if ((st = cached_bluestein((int)n, &en)) != SAR_OK) return st;
+        cudaError_t e = sar::launch_bluestein(*en.d, (const float2 *)in, (float2 *)out, n_lines, n, (int)n, en.filt,
+                                              en.tw, en.chirp, inverse ? 1 : 0, (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "fft launch");
+        return SAR_OK;
+    }
     if ((st = check_length(n, "n")) != SAR_OK) return st;
     if (n_lines < 0) return fail(SAR_ERR_INVALID_ARG, "n_lines < 0");
     if (n_lines == 0) return SAR_OK;
@@ -904,7 +980,7 @@ sar_status sar_fft_lines(int64_t n, int64_t n_lines, const void *in, void *out, 
 
 sar_status sar_make_lfm_spectrum(int64_t n, int64_t n_chirp, double tbp, void *out, sar_stream stream) {
     sar_status st;
-    if ((st = check_length(n, "n")) != SAR_OK) return st;
+    if ((st = check_plan_length(n, "n")) != SAR_OK) return st;
     if (n_chirp < 1 || n_chirp > n) return fail(SAR_ERR_INVALID_ARG, "n_chirp must be in [1, n]");
     if (!(tbp > 0.0)) return fail(SAR_ERR_INVALID_ARG, "tbp must be > 0");
     if ((st = check_device_ptr(out, "out")) != SAR_OK) return st;

@@ -143,6 +143,42 @@ cudaError_t build_wrap_filter(const float2 *H, int n, int L, void *scratch, floa
     return cudaGetLastError();
 }
 
+// --- tables of the DFT of a length that is not a power of two (Bluestein) --
+// chirp[m] = c_m = exp(-i pi m^2 / n) for m < n, the phase reduced exactly as
+// (m^2 mod 2n) / n before sincospi in FP64; b[m] (m < L) = conj(c_{m'}) for the
+// lag m' = m (m < n) or L - m (m > L - n), else 0.
+__global__ void bluestein_chirp_kernel(float2 *chirp, double2 *b, int n, int L) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= L) return;
+    auto c64 = [n](int64_t k) {
+        const int64_t q = (k * k) % (2 * (int64_t)n);
+        double s, c;
+        sincospi(-(double)q / (double)n, &s, &c);
+        return make_double2(c, s);
+    };
+    if (m < n) {
+        const double2 c = c64(m);
+        chirp[m] = make_float2((float)c.x, (float)c.y);
+        b[m] = make_double2(c.x, -c.y);
+    } else if (m > L - n) {
+        const double2 c = c64(L - m);
+        b[m] = make_double2(c.x, -c.y);
+    } else {
+        b[m] = make_double2(0.0, 0.0);
+    }
+}
+
+size_t bluestein_scratch_bytes(int L) { return sizeof(double2) * (size_t)2 * L; }
+
+// chirp (n values) and G = FFT_L(b) (L values, FP64 sums rounded once).
+cudaError_t build_bluestein_tables(int n, int L, float2 *chirp, float2 *G, void *scratch, cudaStream_t st) {
+    double2 *b = (double2 *)scratch, *roots_L = b + L;
+    bluestein_chirp_kernel<<<(L + 255) / 256, 256, 0, st>>>(chirp, b, n, L);
+    roots_f64_kernel<<<(L + 255) / 256, 256, 0, st>>>(roots_L, L, -1);
+    dft_f64_kernel<false><<<(L + 7) / 8, 256, 0, st>>>(b, L, roots_L, L, L, 1.0, nullptr, G);
+    return cudaGetLastError();
+}
+
 cudaError_t build_natural_filter(const float2 *H, float2 *dst, int n, cudaStream_t st) {
     scale_copy_kernel<<<(n + 255) / 256, 256, 0, st>>>(dst, H, n, 1.0f / (float)n);
     return cudaGetLastError();

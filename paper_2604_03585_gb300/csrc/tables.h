@@ -29,6 +29,10 @@ void rd_columns(int n_f, double kappa, double vs, void *host_cols);
 // lines whose length is not a power of two (zero-padded linear convolution)
 size_t wrap_filter_scratch_bytes(int n, int L);
 cudaError_t build_wrap_filter(const float2 *H, int n, int L, void *scratch, float2 *G, cudaStream_t st);
+size_t bluestein_scratch_bytes(int L);
+cudaError_t build_bluestein_tables(int n, int L, float2 *chirp, float2 *G, void *scratch, cudaStream_t st);
+cudaError_t launch_bluestein(const SchedDesc &d, const float2 *in, float2 *out, int64_t n_lines, int64_t ld, int n,
+                             const float2 *filt, const float2 *tw, const float2 *chirp, int inverse, cudaStream_t st);
 size_t rd_column_bytes();
 int corner_turn_variant();
 }  // namespace sar

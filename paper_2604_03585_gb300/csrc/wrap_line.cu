@@ -51,6 +51,79 @@ fused_wrap_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld, in
     }
 }
 
+// The DFT of a line of any length n (Bluestein): with j k = (j^2 + k^2 -
+// (k - j)^2) / 2 and c_m = exp(-i pi m^2 / n),
+//   X[k] = c_k sum_j (x_j c_j) conj(c_{k-j}),
+// a linear convolution of a = x . c (n samples) with conj(c) over lags
+// -(n-1) ... n-1, exact through length-L transforms (L >= 2n - 1) as the
+// first n outputs of IFFT_L(FFT_L(a padded) . G), G = FFT_L(b), b[m mod L] =
+// conj(c_m).  One block per line (LPB lines): the chirped line goes to shared
+// memory, the streamed passes of the length-L engine run in place, the last
+// inverse pass leaves the convolution there, and the store applies c_k.  INV:
+// the inverse kernel as conj(DFT(conj x)).  chirp[m] = c_m, m < n.
+template <class SC, int LPB, bool ROLL, bool INV>
+__global__ void __launch_bounds__(SC::T * LPB)
+bluestein_dft_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld, int n, const float2* filt,
+                     const float2* tw, const float2* chirp) {
+    extern __shared__ float2 smem_dyn[];
+    const int lib = threadIdx.x / SC::T;
+    const int t = threadIdx.x % SC::T;
+    const int64_t line = (int64_t)blockIdx.x * LPB + lib;
+    if (line >= n_lines) return;   // whole line groups only: no barrier is left waiting
+    float2* sm = smem_dyn + lib * SC::SMEM_ELEMS;
+    constexpr int R1 = SC::R1, S1 = SC::S1, G1 = SC::E / R1, RL = SC::RL, GL = SC::E / RL;
+    const float2* src = in + line * ld;
+    for (int j = t; j < SC::N; j += SC::T) {
+        float2 a = make_float2(0.f, 0.f);
+        if (j < n) {
+            float2 x = __ldcs(src + j);
+            if (INV) x.y = -x.y;
+            a = cmul(x, chirp[j]);
+        }
+        sm[smem_pos(j, SC::PADSH)] = a;
+    }
+    line_sync<SC, LPB>(lib);
+    streamed_mid_pass<SC, R1, S1, false, ROLL>(sm, tw, t);
+    line_sync<SC, LPB>(lib);
+    const float2* tw2 = tw + R1 * S1;
+    if constexpr (SC::P == 3) {
+        streamed_mid_pass<SC, SC::R2, SC::S2, false, ROLL>(sm, tw2, t);
+        line_sync<SC, LPB>(lib);
+    }
+#pragma unroll(ROLL ? 1 : GL)
+    for (int s = 0; s < GL; ++s) {
+        const int g = t + SC::T * s;
+        float2 x[RL];
+        grp_smem_load<RL, 1>(sm, g * RL, SC::PADSH, x);
+        dft_reg<RL, false>(x);
+#pragma unroll
+        for (int r = 0; r < RL; ++r) x[r] = cmul(x[r], filt[(s * RL + r) * SC::T + t]);
+        dft_reg<RL, true>(x);
+        grp_smem_store<RL, 1>(sm, g * RL, SC::PADSH, x);
+    }
+    line_sync<SC, LPB>(lib);
+    if constexpr (SC::P == 3) {
+        streamed_mid_pass<SC, SC::R2, SC::S2, true, ROLL>(sm, tw2, t);
+        line_sync<SC, LPB>(lib);
+    }
+#pragma unroll(ROLL ? 1 : G1)
+    for (int s = 0; s < G1; ++s) {
+        const int lo = t + SC::T * s;
+        float2 x[R1];
+        grp_smem_load<R1, S1>(sm, lo, SC::PADSH, x);
+        grp_twiddle<R1, S1, true>(tw, lo, x);
+        dft_reg<R1, true>(x);
+        grp_smem_store<R1, S1>(sm, lo, SC::PADSH, x);
+    }
+    line_sync<SC, LPB>(lib);
+    float2* dst = out + line * (int64_t)n;   // outputs are dense lines of n
+    for (int k = t; k < n; k += SC::T) {
+        float2 y = cmul(sm[smem_pos(k, SC::PADSH)], chirp[k]);
+        if (INV) y.y = -y.y;
+        __stcs(dst + k, y);
+    }
+}
+
 namespace {
 
 template <class SC, int LPB, bool ROLL>
@@ -111,6 +184,49 @@ const SchedDesc* wrap_schedule(int L) {
     for (const SchedDesc& d : kWrap)
         if (d.n == L) return &d;
     return nullptr;
+}
+
+namespace {
+template <class SC, int LPB, bool ROLL>
+cudaError_t launch_bluestein_t(const float2* in, float2* out, int64_t n_lines, int64_t ld, int n, const float2* filt,
+                               const float2* tw, const float2* chirp, int inverse, cudaStream_t st) {
+    constexpr int smem = smem_bytes_of<SC, LPB>();
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(bluestein_dft_kernel<SC, LPB, ROLL, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(bluestein_dft_kernel<SC, LPB, ROLL, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+    }
+    const unsigned blocks = (unsigned)((n_lines + LPB - 1) / LPB);
+    if (inverse)
+        bluestein_dft_kernel<SC, LPB, ROLL, true><<<blocks, SC::T * LPB, smem, st>>>(in, out, n_lines, ld, n, filt,
+                                                                                   tw, chirp);
+    else
+        bluestein_dft_kernel<SC, LPB, ROLL, false><<<blocks, SC::T * LPB, smem, st>>>(in, out, n_lines, ld, n, filt,
+                                                                                    tw, chirp);
+    return cudaGetLastError();
+}
+}  // namespace
+
+// The DFT of n_lines lines of a length n that is not a power of two (2 <= n,
+// 2n - 1 <= L), through the wrap schedule of engine length L = d.n and its
+// tables: filt = G / L in the engine's register order, chirp[m] = c_m.
+cudaError_t launch_bluestein(const SchedDesc& d, const float2* in, float2* out, int64_t n_lines, int64_t ld, int n,
+                             const float2* filt, const float2* tw, const float2* chirp, int inverse, cudaStream_t st) {
+    if (n_lines <= 0) return cudaSuccess;
+    if (n < 2 || 2 * (int64_t)n - 1 > d.n || ld < n) return cudaErrorInvalidValue;
+    switch (d.n) {
+        case 256: return launch_bluestein_t<Sched<256, 16, 16, 16>, 8, false>(in, out, n_lines, ld, n, filt, tw, chirp, inverse, st);
+        case 512: return launch_bluestein_t<Sched<512, 32, 16, 32>, 8, false>(in, out, n_lines, ld, n, filt, tw, chirp, inverse, st);
+        case 1024: return launch_bluestein_t<Sched<1024, 32, 32, 32>, 4, false>(in, out, n_lines, ld, n, filt, tw, chirp, inverse, st);
+        case 2048: return launch_bluestein_t<Sched<2048, 16, 16, 8, 16>, 1, false>(in, out, n_lines, ld, n, filt, tw, chirp, inverse, st);
+        case 4096: return launch_bluestein_t<Sched<4096, 32, 16, 16, 16>, 1, true>(in, out, n_lines, ld, n, filt, tw, chirp, inverse, st);
+        case 8192: return launch_bluestein_t<Sched<8192, 32, 16, 16, 32>, 1, true>(in, out, n_lines, ld, n, filt, tw, chirp, inverse, st);
+        case 16384: return launch_bluestein_t<Sched<16384, 32, 16, 32, 32>, 1, true>(in, out, n_lines, ld, n, filt, tw, chirp, inverse, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace sar

@@ -146,3 +146,38 @@ def test_any_length_refusals(sar):
         sar.sar_rda_full(plan, x, torch.empty_like(img), torch.empty_like(img))
     assert e.value.status == sar.SAR_ERR_UNSUPPORTED
     plan.destroy()
+
+
+# ---------------------------------------------------------------------------
+# the DFT itself at any length (Bluestein on the power-of-two engine)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [2, 3, 5, 100, 127, 128, 255, 1000, 3000, 5000, 8191])
+@pytest.mark.parametrize("inverse", [False, True], ids=["fwd", "inv"])
+def test_fft_any_length_vs_oracle(sar, orc, n, inverse):
+    """sar_fft_lines at lengths that are not powers of two (or below 256)
+    against the oracle's DFT, which at such lengths is the definition's sum."""
+    x = noise(97 + n, 3, n)
+    ref = np.stack([orc.fft(row, inverse=inverse) for row in x])
+    xd = dev(x)
+    out = torch.empty_like(xd)
+    sar.sar_fft_lines(n, 3, xd, out, inverse)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    err = M.rel_l2(got, ref)
+    print(f"\nBLUESTEIN n={n} {'inv' if inverse else 'fwd'}: rel_l2 {err:.2e}")
+    assert err < 2e-6
+    assert np.array_equal(xd.cpu().numpy(), x.astype(np.complex64))
+    sar.sar_fft_lines(n, 3, xd, xd, inverse)                     # in place
+    torch.cuda.synchronize()
+    assert np.array_equal(xd.cpu().numpy(), got)
+
+
+@pytest.mark.parametrize("n", [100, 1000, 3000])
+def test_lfm_spectrum_any_length(sar, orc, n):
+    nc, tbp = n // 4, n / 8.0
+    H = torch.empty(n, dtype=torch.complex64, device="cuda")
+    sar.sar_make_lfm_spectrum(n, nc, tbp, H)
+    torch.cuda.synchronize()
+    ref = orc.matched_filter(n, sarsim.lfm_chirp(nc, tbp))
+    assert M.rel_l2(H.cpu().numpy(), ref) < 2e-6
