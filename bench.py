@@ -518,6 +518,17 @@ def any_length_bench(sar, dev, stream, peak, reps: int = 20) -> dict:
         gbs = 16.0 * n * n_lines / (ms * 1e-3) / 1e9
         out[str(n)] = {"engine_length": L, "lines": n_lines, "ms": ms, "gb_s": gbs, "frac_hbm": gbs / peak}
         plan.destroy()
+        # the DFT alone at the same length (Bluestein when n is not a power of two)
+        times = []
+        for i in range(reps + 3):
+            e0.record(stream)
+            sar.sar_fft_lines(n, n_lines, data, data, False, stream)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= 3:
+                times.append(e0.elapsed_time(e1))
+        times.sort()
+        out[str(n)]["fft_gb_s"] = 16.0 * n * n_lines / (times[len(times) // 2] * 1e-3) / 1e9
         del data
     return out
 
