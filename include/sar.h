@@ -303,7 +303,7 @@ typedef struct {
     const void *raw;            /* device complex64[n_az][n_range], read only */
     void *image;                /* device complex64[n_range][n_az], output */
     const void *range_spectrum; /* device complex64[n_range] */
-    const void *az_spectrum;    /* device complex64[L] */
+    const void *az_spectrum;    /* device complex64[L] (complex64[n_az] with SAR_BATCH_EXACT_AZIMUTH) */
 } sar_strip;
 
 typedef struct sar_batch_s *sar_batch;
@@ -322,7 +322,15 @@ typedef struct {
  * and twiddle tables and segment table, allocate the work buffer
  * (8 bytes per raw sample) and capture the whole batch into one CUDA graph.
  * The strip buffers stay owned by the caller and must outlive the batch; the
- * spectra are copied.  flags must be 0.  Synchronises the device. */
+ * spectra are copied.  flags: 0 or SAR_BATCH_EXACT_AZIMUTH.  Synchronises the
+ * device. */
+/* Azimuth lines compressed at exactly their n_az samples (the circular
+ * correlation at n_az, as a plan of that length computes it) instead of
+ * zero-padded to L: az_spectrum holds n_az values, classes are (n_az, azimuth
+ * spectrum), and a length that is not a power of two (at most 8192) runs the
+ * zero-padded linear convolution of sar_plan_create, one launch per strip in
+ * the graph. */
+#define SAR_BATCH_EXACT_AZIMUTH 1u
 SAR_API sar_status sar_batch_create(const sar_strip *strips, int32_t count, uint32_t flags, sar_batch *out);
 
 /* Compress every strip of the batch: one graph launch on `stream` (range

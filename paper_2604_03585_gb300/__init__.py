@@ -28,6 +28,7 @@ SAR_OK, SAR_ERR_INVALID_ARG, SAR_ERR_UNSUPPORTED, SAR_ERR_OUT_OF_MEMORY, SAR_ERR
 SAR_PREC_FP32, SAR_PREC_FP16X2, SAR_PREC_BF16X2, SAR_PREC_BF16X3 = 0, 1, 2, 3
 SAR_PLAN_UNFOLDED_CORNER_TURN = 1
 SAR_PLAN_OUT_AZ_MAJOR = 2
+SAR_BATCH_EXACT_AZIMUTH = 1
 SAR_TUNE_FUSED, SAR_TUNE_RANGE_CT = 0, 1
 SAR_SERVE_OPEN_LOOP, SAR_SERVE_CLOSED_LOOP = 0, 1
 

@@ -80,6 +80,7 @@ struct LineClass {
     const void *spectrum = nullptr;
     int64_t n = 0;
     bool ragged = false;
+    bool wrap = false;   // exact length n that is not a power of two: wrap schedule of length d->n
     std::vector<sar::Seg> segs;
     std::vector<int64_t> begin;   // prefix sums of lines, size segs + 1
     // device
@@ -130,7 +131,8 @@ sar_status sar_batch_create(const sar_strip *strips, int32_t count, uint32_t fla
     if (!out) return sar::report_error(SAR_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!strips || count < 1) return sar::report_error(SAR_ERR_INVALID_ARG, "need at least one strip");
-    if (flags != 0) return sar::report_error(SAR_ERR_INVALID_ARG, "flags must be 0");
+    if (flags & ~SAR_BATCH_EXACT_AZIMUTH) return sar::report_error(SAR_ERR_INVALID_ARG, "unknown flags");
+    const bool exact = (flags & SAR_BATCH_EXACT_AZIMUTH) != 0;
     sar_status st;
     for (int32_t i = 0; i < count; ++i) {
         const sar_strip &s = strips[i];
@@ -139,6 +141,10 @@ sar_status sar_batch_create(const sar_strip *strips, int32_t count, uint32_t fla
             return sar::report_error(SAR_ERR_UNSUPPORTED, "strip n_range must be at most 16384");
         if (s.n_az < 1 || s.n_az > 16384)
             return sar::report_error(SAR_ERR_UNSUPPORTED, "strip n_az must be in [1, 16384]");
+        const bool az_pow2 = s.n_az >= 256 && (s.n_az & (s.n_az - 1)) == 0;
+        if (exact && !az_pow2 && (s.n_az < 2 || s.n_az > 8192))
+            return sar::report_error(SAR_ERR_UNSUPPORTED,
+                                     "exact azimuth lengths that are not powers of two must be in [2, 8192]");
         if ((st = sar::validate_device_ptr(s.raw, "strip raw")) != SAR_OK) return st;
         if ((st = sar::validate_device_ptr(s.image, "strip image")) != SAR_OK) return st;
         if ((st = sar::validate_device_ptr(s.range_spectrum, "strip range_spectrum")) != SAR_OK) return st;
@@ -168,7 +174,7 @@ sar_status sar_batch_create(const sar_strip *strips, int32_t count, uint32_t fla
     };
     for (int32_t i = 0; i < count; ++i) {
         const sar_strip &s = strips[i];
-        const int64_t L = std::max<int64_t>(256, next_pow2(s.n_az));
+        const int64_t L = exact ? s.n_az : std::max<int64_t>(256, next_pow2(s.n_az));
         if (L > 16384) {
             batch_free(b);
             return sar::report_error(SAR_ERR_UNSUPPORTED, "azimuth transform length above 16384");
@@ -181,13 +187,20 @@ sar_status sar_batch_create(const sar_strip *strips, int32_t count, uint32_t fla
         ac.segs.push_back(sar::Seg{(const float2 *)s.image, (float2 *)s.image, s.n_az, s.n_az, (int32_t)s.n_az, 0});
         ac.begin.push_back(ac.begin.back() + s.n_range);
         if (s.n_az < L) ac.ragged = true;
+        if (exact && !(L >= 256 && (L & (L - 1)) == 0)) ac.wrap = true;
         b->tsegs.push_back(sar::TSeg{nullptr, (float2 *)s.image, s.n_az, s.n_range, (s.n_range + 31) / 32});
     }
     b->tbegin.push_back(0);
     for (auto &t : b->tsegs) b->tbegin.push_back(b->tbegin.back() + ((t.rows + 31) / 32) * t.tiles_c);
     for (auto *cls : {&b->range, &b->az})
         for (auto &c : *cls) {
-            c.d = seg_schedule((int)c.n);
+            if (c.wrap) {
+                int64_t L = 256;
+                while (L < 2 * c.n - 1) L <<= 1;
+                c.d = sar::wrap_schedule((int)L);
+            } else {
+                c.d = seg_schedule((int)c.n);
+            }
             if (!c.d) {
                 batch_free(b);
                 return sar::report_error(SAR_ERR_UNSUPPORTED, "no segment-table kernel for a strip length");
@@ -205,11 +218,11 @@ sar_status sar_batch_create(const sar_strip *strips, int32_t count, uint32_t fla
     int64_t max_n = 0;
     for (auto *cls : {&b->range, &b->az})
         for (auto &c : *cls) {
-            off_f.push_back(reserve(sizeof(float2) * c.n));
+            off_f.push_back(reserve(sizeof(float2) * c.d->n));
             off_t.push_back(reserve(sizeof(float2) * c.d->tw_elems));
             off_s.push_back(reserve(sizeof(sar::Seg) * c.segs.size()));
             off_b.push_back(reserve(sizeof(int64_t) * c.begin.size()));
-            max_n = std::max(max_n, c.n);
+            max_n = std::max<int64_t>(max_n, c.d->n);
         }
     const size_t off_ts = reserve(sizeof(sar::TSeg) * b->tsegs.size());
     const size_t off_tb = reserve(sizeof(int64_t) * b->tbegin.size());
@@ -254,11 +267,30 @@ sar_status sar_batch_create(const sar_strip *strips, int32_t count, uint32_t fla
             ++ci;
             if ((e = c.d->prepare()) != cudaSuccess) break;
             if ((e = sar::build_twiddles(*c.d, c.tw, s)) != cudaSuccess) break;
-            idx.assign(c.n, 0);
+            idx.assign(c.d->n, 0);
             sar::filter_slot_to_k(*c.d, idx.data());
-            if ((e = cudaMemcpyAsync(idx_dev, idx.data(), sizeof(int32_t) * c.n, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            if ((e = cudaMemcpyAsync(idx_dev, idx.data(), sizeof(int32_t) * c.d->n, cudaMemcpyHostToDevice, s)) !=
+                cudaSuccess)
                 break;
-            if ((e = sar::build_filter(*c.d, (const float2 *)c.spectrum, c.filt, idx_dev, s)) != cudaSuccess) break;
+            const float2 *spectrum = (const float2 *)c.spectrum;
+            void *design = nullptr;
+            if (c.wrap) {
+                // G = FFT_L(IFFT_n(H) zero-padded to L), designed in FP64
+                const size_t scratch = sar::wrap_filter_scratch_bytes((int)c.n, c.d->n);
+                if ((e = cudaMalloc(&design, scratch + sizeof(float2) * (size_t)c.d->n)) != cudaSuccess) break;
+                float2 *G = (float2 *)((char *)design + scratch);
+                if ((e = sar::build_wrap_filter(spectrum, (int)c.n, c.d->n, design, G, s)) != cudaSuccess) {
+                    cudaFree(design);
+                    break;
+                }
+                spectrum = G;
+            }
+            e = sar::build_filter(*c.d, spectrum, c.filt, idx_dev, s);
+            if (design) {
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                cudaFree(design);
+            }
+            if (e != cudaSuccess) break;
             if ((e = cudaMemcpyAsync(c.segs_dev, c.segs.data(), sizeof(sar::Seg) * c.segs.size(), cudaMemcpyHostToDevice,
                                      s)) != cudaSuccess)
                 break;
@@ -291,7 +323,17 @@ sar_status sar_batch_create(const sar_strip *strips, int32_t count, uint32_t fla
             le = cudaGetLastError();
             ++b->launches;
         }
+        const sar::FusedCtl no_ctl{nullptr, 0, -1};
         for (auto &c : b->az) {
+            if (c.wrap) {   // one launch per strip of this exact length
+                for (size_t k = 0; k < c.segs.size() && le == cudaSuccess; ++k) {
+                    const sar::Seg &sg = c.segs[k];
+                    le = c.d->fused(sg.in, sg.out, c.begin[k + 1] - c.begin[k], sg.ld_in, sg.valid, c.filt, c.tw,
+                                    no_ctl, s);
+                    ++b->launches;
+                }
+                continue;
+            }
             if (le == cudaSuccess)
                 le = c.d->fused_seg(c.segs_dev, c.begin_dev, (int)c.segs.size(), c.begin.back(), c.ragged, c.filt, c.tw,
                                     s);

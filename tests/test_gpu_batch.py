@@ -104,3 +104,54 @@ def test_batch_refuses_bad_strips(sar):
     with pytest.raises(sar.SarError):
         sar.sar_batch_create([dict(n_range=256, n_az=4, raw=np.zeros(4, np.complex64), image=x,
                                    range_spectrum=x, az_spectrum=x)])
+
+
+def test_ragged_batch_exact_azimuth_vs_oracle(sar):
+    """SAR_BATCH_EXACT_AZIMUTH: every strip's azimuth lines compressed at
+    exactly n_az (the oracle's circular correlation at that length; no zero
+    padding), with azimuth spectra of n_az values."""
+    orc = oracle.default()
+    shapes = [(1024, 300), (256, 256), (2048, 777), (1024, 1000), (512, 129), (256, 77), (1024, 300), (512, 128)]
+    strips, keep, specs, refs = [], [], [], []
+    hr, ha = {}, {}
+    for i, (n_range, n_az) in enumerate(shapes):
+        (ncr, tbr), _ = sarsim.scaled_chirps(n_range, 256)
+        nca = max(4, n_az // 4)
+        tba = max(1.0, nca / 8.0)
+        targets = [(n_az // 2, n_range // 2)]
+        spec = sarsim.SceneSpec(n_az=n_az, n_range=n_range, targets=targets, range_chirp=(ncr, tbr),
+                                az_chirp=(nca, tba), snr_db=20.0, seed=60 + i)
+        raw = sarsim.echo(spec)
+        if n_range not in hr:
+            hr[n_range] = orc.matched_filter(n_range, sarsim.lfm_chirp(ncr, tbr))
+        key = (n_az, nca)
+        if key not in ha:
+            ha[key] = orc.matched_filter(n_az, sarsim.lfm_chirp(nca, tba))
+        raw_d = torch.from_numpy(raw).cuda()
+        img_d = torch.empty((n_range, n_az), dtype=torch.complex64, device="cuda")
+        strips.append(dict(n_range=n_range, n_az=n_az, raw=raw_d, image=img_d,
+                           range_spectrum=torch.from_numpy(hr[n_range].astype(np.complex64)).cuda(),
+                           az_spectrum=torch.from_numpy(ha[key].astype(np.complex64)).cuda()))
+        keep.append((raw, raw_d, img_d, strips[-1]))
+        specs.append(spec)
+        refs.append(orc.rda(raw, hr[n_range].astype(np.complex64).astype(np.complex128),
+                            ha[key].astype(np.complex64).astype(np.complex128), nthreads=NTHREADS))
+    batch = sar.sar_batch_create(strips, flags=sar.SAR_BATCH_EXACT_AZIMUTH)
+    info = sar.sar_batch_info(batch)
+    assert info["strips"] == len(shapes)
+    sar.sar_batch_run(batch)
+    sar.sar_sync()
+    for (raw, raw_d, img_d, _), spec, ref in zip(keep, specs, refs):
+        img = img_d.cpu().numpy()
+        assert np.array_equal(raw_d.cpu().numpy(), raw)
+        err = M.rel_l2(img, ref)
+        print(f"\nEXACT {spec.n_range}x{spec.n_az}: rel_l2 {err:.2e}")
+        assert err < 2e-5, (spec.n_range, spec.n_az)
+        (a0, r0), = spec.targets
+        assert M.peak(img, (r0, a0)) == M.peak(ref, (r0, a0)) == (r0, a0)
+    batch.destroy()
+    x = torch.empty(16, dtype=torch.complex64, device="cuda")
+    with pytest.raises(sar.SarError) as e:
+        sar.sar_batch_create([dict(n_range=256, n_az=9000, raw=x, image=x, range_spectrum=x, az_spectrum=x)],
+                             flags=sar.SAR_BATCH_EXACT_AZIMUTH)
+    assert e.value.status == sar.SAR_ERR_UNSUPPORTED
