@@ -36,6 +36,10 @@ N_AZ = N_RANGE = 4096
 N_RAW_BUFFERS = 4
 
 
+EXTRAS = ("passes", "scene_256", "pipelined", "az_major", "unfused", "precision", "rda_full", "long_lines",
+          "any_length", "ragged_batch", "serving")
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -48,11 +52,13 @@ def parse():
     ap.add_argument("--azimuth-schedule", default=None, help="schedule of the azimuth pass (default: autotuned)")
     ap.add_argument("--no-autotune", action="store_true", help="use the compiled-in preferred schedules")
     ap.add_argument("--no-extras", action="store_true", help="skip the ragged-batch and serving measurements")
-    ap.add_argument("--extras",
-                    default="passes,scene_256,pipelined,az_major,unfused,precision,rda_full,long_lines,any_length,"
-                            "ragged_batch,serving",
+    ap.add_argument("--extras", default=",".join(EXTRAS),
                     help="comma-separated extra measurements to run after the headline step")
-    return ap.parse_args()
+    args = ap.parse_args()
+    unknown = {x.strip() for x in args.extras.split(",") if x.strip()} - set(EXTRAS)
+    if unknown:
+        ap.error(f"unknown --extras {sorted(unknown)}; choose from {', '.join(EXTRAS)}")
+    return args
 
 
 def measured_peaks() -> dict:
@@ -867,10 +873,6 @@ def main():
 
     extras = {}
     wanted = set() if args.no_extras else {x.strip() for x in args.extras.split(",") if x.strip()}
-    unknown = wanted - {"passes", "scene_256", "pipelined", "az_major", "unfused", "precision", "rda_full",
-                        "long_lines", "any_length", "ragged_batch", "serving"}
-    if unknown:
-        raise SystemExit(f"bench.py: unknown extras {sorted(unknown)}")
     if "passes" in wanted:
         extras["passes"] = passes_bench(sar, Hr, Ha, raws, work, image, stream)
     if "scene_256" in wanted:

@@ -53,7 +53,8 @@ def test_argument_errors_without_gpu(sar):
     f4 = sar.sar_filters(None, None, sar.SAR_PREC_FP16X2, 0)   # split precision: 256 / 4096 only
     assert lib.sar_plan_create(1024, 256, ctypes.byref(f4), ctypes.byref(h)) == sar.SAR_ERR_UNSUPPORTED
     assert h.value is None
-    assert lib.sar_fft_lines(100, 1, None, None, 0, None) == sar.SAR_ERR_UNSUPPORTED
+    assert lib.sar_fft_lines(10000, 1, None, None, 0, None) == sar.SAR_ERR_UNSUPPORTED   # above 8192, not 2^k
+    assert lib.sar_fft_lines(100, 1, None, None, 0, None) == sar.SAR_ERR_INVALID_ARG     # any length: bad pointers
     assert lib.sar_fft_lines(256, -1, None, None, 0, None) == sar.SAR_ERR_INVALID_ARG
     assert lib.sar_fft_lines(256, 0, None, None, 0, None) == sar.SAR_OK   # nothing to do
     assert lib.sar_make_lfm_spectrum(256, 0, 1.0, None, None) == sar.SAR_ERR_INVALID_ARG
@@ -90,3 +91,25 @@ def test_traffic_convention_reproduces_range_step(sar):
     assert abs(t_min - float(min_ms)) < 0.1
     assert roofline.rda_bytes(4096, 4096) == 805306368
     assert roofline.fused_line_flops(4096) == 516096
+
+
+def test_binding_constants_match_the_header(sar):
+    """Every #define of include/sar.h has the same value in the binding."""
+    text = open(os.path.join(ROOT, "include", "sar.h")).read()
+    defines = dict(re.findall(r"#define\s+(SAR_[A-Z0-9_]+)\s+(\d+)u?\b", text))
+    assert defines, "no constants found"
+    for name, value in defines.items():
+        assert getattr(sar, name) == int(value), name
+
+
+def test_bench_refuses_unknown_extras(monkeypatch):
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--extras", "no_such_section"])
+    with pytest.raises(SystemExit):
+        bench.parse()                      # refused before any GPU work
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    every = set(bench.parse().extras.split(","))
+    assert {"passes", "scene_256", "pipelined", "az_major", "unfused", "precision", "rda_full", "long_lines",
+            "any_length", "ragged_batch", "serving"} == every
