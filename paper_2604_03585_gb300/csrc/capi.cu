@@ -837,14 +837,12 @@ sar_status sar_rda_full(sar_plan p, const void *raw, void *work, void *image, sa
     const char *az_name = sar::rd_az_schedule((int)p->n_az);
     const SchedDesc *dz = az_name ? sar::find_schedule(az_name) : nullptr;
     if (!dz) return fail(SAR_ERR_UNSUPPORTED, "full processing needs n_az <= 16384");
-    const SchedDesc &da = *p->az.sched;
-    float2 *tw_fft = nullptr, *tw_az = nullptr;
-    if ((st = cached_twiddles(&da, &tw_fft)) != SAR_OK) return st;
+    float2 *tw_az = nullptr;
     if ((st = cached_twiddles(dz, &tw_az)) != SAR_OK) return st;
     // 1. range compression and corner turn: raw -> image [n_range][n_az]
     if ((st = sar_rda_process_oop_range(p, raw, work, image, s)) != SAR_OK) return st;
     // 2. azimuth FFT of every range bin, in place
-    cudaError_t e = da.dft((const float2 *)image, (float2 *)image, p->n_range, p->n_az, (int)p->n_az, tw_fft, 0, s);
+    cudaError_t e = sar::launch_az_fft_rd((int)p->n_az, (const float2 *)image, (float2 *)image, p->n_range, tw_az, s);
     if (e != cudaSuccess) return cuda_fail(e, "azimuth FFT launch");
     // 3. RCMC image -> work (or no correction: work <- image)
     if (p->taps)

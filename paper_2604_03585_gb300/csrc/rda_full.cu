@@ -19,7 +19,7 @@
 // range bin n never enters a rounded sum (at n ~ 8000 the FP32 spacing is
 // 1e-3 samples, which would cost ~1e-3 relative error on a half-band signal).
 #include "../../include/sar.h"
-#include "line_engine.cuh"
+#include "streamed.cuh"
 #include "registry.h"
 #include "tables.h"
 
@@ -181,48 +181,88 @@ rcmc_tile_kernel(const float2* __restrict__ in, float2* __restrict__ out, int n_
     }
 }
 
-// Azimuth compression of range bin `line` (r = r_near + line): multiply the
-// natural-order spectrum by exp(+2 pi i kappa r D(f_j)), inverse FFT through
-// conj(FFT(conj .)) (Sec. II-C), 1/N, natural-order coalesced store.
-template <class SC>
+// The azimuth kernels of the full processor in group-streamed form: the passes
+// before the last run one radix group at a time (R values live, the next
+// group's loads in flight during the current group's arithmetic); the last
+// pass keeps the line in registers for the scatter to natural order through
+// shared memory and the coalesced store.  COMPRESS (range bin `line`,
+// r = r_near + line): every sample j is first multiplied by
+// exp(+2 pi i frac(kappa r D(f_j))) -- the phase of up to ~1e5 cycles formed
+// by an FP32 two-product of r with kappa D(f_j) held as hi + lo, so that only
+// its fractional part is rounded -- and conjugated, and the store conjugates
+// and scales by 1/N: the inverse FFT of the filtered line through
+// conj(FFT(conj .)) (Sec. II-C).  Otherwise the forward FFT of the line (the
+// Range-Doppler domain, Sec. IV-A step 2).
+template <class SC, bool COMPRESS>
 __global__ void __launch_bounds__(SC::T)
-az_compress_rd_kernel(const float2* in, float2* out, int64_t n_lines, const float2* tw, const RdColumn* cols,
-                      double r_near) {
+az_streamed_kernel(const float2* in, float2* out, int64_t n_lines, const float2* tw, const RdColumn* cols,
+                   double r_near) {
     extern __shared__ float2 smem_dyn[];
     const int t = threadIdx.x;
     const int64_t line = blockIdx.x;
     if (line >= n_lines) return;
     float2* sm = smem_dyn;
-    const double rd = r_near + (double)line;
-    const float r_hi = (float)rd, r_lo = (float)(rd - (double)r_hi);
-    float2 v[SC::E];
+    constexpr int R1 = SC::R1, S1 = SC::S1, G1 = SC::E / R1, RL = SC::RL, GL = SC::E / RL;
     const float2* src = in + line * SC::N;
-#pragma unroll
-    for (int s = 0; s < SC::E / SC::R1; ++s) {
-        const int lo = t + SC::T * s;
-#pragma unroll
-        for (int r = 0; r < SC::R1; ++r) {
-            const int j = lo + r * SC::S1;
+    float r_hi = 0.f, r_lo = 0.f;
+    if constexpr (COMPRESS) {
+        const double rd = r_near + (double)line;
+        r_hi = (float)rd;
+        r_lo = (float)(rd - (double)r_hi);
+    }
+    auto sample = [&](int j) -> float2 {
+        float2 x = __ldcs(src + j);
+        if constexpr (COMPRESS) {
             const RdColumn c = cols[j];
-            const float p = __fmul_rn(r_hi, c.a_hi);          // never contracted into p - rint(p)
-            const float e = fmaf(r_hi, c.a_hi, -p);           // exact error of the product
+            const float p = __fmul_rn(r_hi, c.a_hi);   // never contracted into p - rint(p)
+            const float e = fmaf(r_hi, c.a_hi, -p);    // exact error of the product
             const float frac = (p - rintf(p)) + (e + fmaf(r_hi, c.a_lo, r_lo * c.a_hi));
             float sn, cs;
             sincospif(2.f * frac, &sn, &cs);
-            const float2 x = __ldcs(src + j);
-            // x * exp(+i phase), conjugated for the forward-transform inverse
-            v[s * SC::R1 + r] = cconj(make_float2(fmaf(x.x, cs, -x.y * sn), fmaf(x.x, sn, x.y * cs)));
+            x = cconj(make_float2(fmaf(x.x, cs, -x.y * sn), fmaf(x.x, sn, x.y * cs)));
+        }
+        return x;
+    };
+    // pass 1: HBM -> (phase) -> DFT -> twiddle -> shared memory
+    float2 cur[R1];
+#pragma unroll
+    for (int r = 0; r < R1; ++r) cur[r] = sample(t + r * S1);
+#pragma unroll
+    for (int s = 0; s < G1; ++s) {
+        const int lo = t + SC::T * s;
+        float2 nxt[R1];
+        if (s + 1 < G1) {
+#pragma unroll
+            for (int r = 0; r < R1; ++r) nxt[r] = sample(lo + SC::T + r * S1);
+        }
+        dft_reg<R1, false>(cur);
+        grp_twiddle<R1, S1, false>(tw, lo, cur);
+        grp_smem_store<R1, S1>(sm, lo, SC::PADSH, cur);
+        if (s + 1 < G1) {
+#pragma unroll
+            for (int r = 0; r < R1; ++r) cur[r] = nxt[r];
         }
     }
-    forward_passes<SC, 1>(v, sm, tw, t, 0);
+    __syncthreads();
+    if constexpr (SC::P == 3) {
+        streamed_mid_pass<SC, SC::R2, SC::S2, false, true>(sm, tw + R1 * S1, t);
+        __syncthreads();
+    }
+    // last pass into registers, then natural order through shared memory
+    float2 v[SC::E];
+#pragma unroll
+    for (int s = 0; s < GL; ++s) {
+        float2 x[RL];
+        grp_smem_load<RL, 1>(sm, (t + SC::T * s) * RL, SC::PADSH, x);
+        dft_reg<RL, false>(x);
+#pragma unroll
+        for (int r = 0; r < RL; ++r) v[s * RL + r] = x[r];
+    }
     __syncthreads();
 #pragma unroll
-    for (int s = 0; s < SC::E / SC::RL; ++s) {
+    for (int s = 0; s < GL; ++s) {
 #pragma unroll
-        for (int r = 0; r < SC::RL; ++r) {
-            const int k = natural_index<SC>(t + SC::T * s, r);
-            sm[smem_pos(k, SC::PADSH)] = v[s * SC::RL + r];
-        }
+        for (int r = 0; r < RL; ++r) sm[smem_pos(natural_index<SC>(t + SC::T * s, r), SC::PADSH)] = v[s * RL + r];
     }
     __syncthreads();
     constexpr float inv_n = 1.0f / SC::N;
@@ -231,7 +271,7 @@ az_compress_rd_kernel(const float2* in, float2* out, int64_t n_lines, const floa
     for (int i = 0; i < SC::E; ++i) {
         const int k = t + SC::T * i;
         const float2 x = sm[smem_pos(k, SC::PADSH)];
-        __stcs(dst + k, make_float2(x.x * inv_n, -x.y * inv_n));
+        __stcs(dst + k, COMPRESS ? make_float2(x.x * inv_n, -x.y * inv_n) : x);
     }
 }
 
@@ -239,22 +279,37 @@ namespace {
 using A256 = Sched<256, 16, 16, 16>;
 using A512 = Sched<512, 32, 16, 32>;
 using A1024 = Sched<1024, 32, 32, 32>;
-using A2048 = Sched<2048, 16, 16, 16, 8>;
+using A2048 = Sched<2048, 16, 16, 8, 16>;
 using A4096 = Sched<4096, 32, 16, 16, 16>;
 using A8192 = Sched<8192, 32, 16, 16, 32>;
 using A16384 = Sched<16384, 32, 16, 32, 32>;
 
-template <class SC>
+template <class SC, bool COMPRESS>
 cudaError_t launch_az(const float2* in, float2* out, int64_t n_lines, const float2* tw, const RdColumn* cols,
                       double r_near, cudaStream_t st) {
     constexpr int smem = SC::SMEM_ELEMS * 8;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(az_compress_rd_kernel<SC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             smem);
+        cudaError_t e = cudaFuncSetAttribute(az_streamed_kernel<SC, COMPRESS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
     }
-    az_compress_rd_kernel<SC><<<(unsigned)n_lines, SC::T, smem, st>>>(in, out, n_lines, tw, cols, r_near);
+    az_streamed_kernel<SC, COMPRESS><<<(unsigned)n_lines, SC::T, smem, st>>>(in, out, n_lines, tw, cols, r_near);
     return cudaGetLastError();
+}
+
+template <bool COMPRESS>
+cudaError_t launch_az_n(int n, const float2* in, float2* out, int64_t n_lines, const float2* tw, const RdColumn* c,
+                        double r_near, cudaStream_t st) {
+    switch (n) {
+        case 256: return launch_az<A256, COMPRESS>(in, out, n_lines, tw, c, r_near, st);
+        case 512: return launch_az<A512, COMPRESS>(in, out, n_lines, tw, c, r_near, st);
+        case 1024: return launch_az<A1024, COMPRESS>(in, out, n_lines, tw, c, r_near, st);
+        case 2048: return launch_az<A2048, COMPRESS>(in, out, n_lines, tw, c, r_near, st);
+        case 4096: return launch_az<A4096, COMPRESS>(in, out, n_lines, tw, c, r_near, st);
+        case 8192: return launch_az<A8192, COMPRESS>(in, out, n_lines, tw, c, r_near, st);
+        case 16384: return launch_az<A16384, COMPRESS>(in, out, n_lines, tw, c, r_near, st);
+    }
+    return cudaErrorInvalidValue;
 }
 }  // namespace
 
@@ -264,7 +319,7 @@ const char* rd_az_schedule(int n) {
         case 256: return "n256_e16_r16x16_l8";
         case 512: return "n512_e32_r16x32_l8";
         case 1024: return "n1024_e32_r32x32_l4";
-        case 2048: return "n2048_e16_r16x16x8_l1";
+        case 2048: return "n2048_e16_r16x8x16_l1";
         case 4096: return "n4096_e32_r16x16x16_l1";
         case 8192: return "n8192_e32_r16x16x32_l1";
         case 16384: return "n16384_e32_r16x32x32_l1";
@@ -274,17 +329,14 @@ const char* rd_az_schedule(int n) {
 
 cudaError_t launch_az_compress_rd(int n, const float2* in, float2* out, int64_t n_lines, const float2* tw,
                                   const void* cols, double r_near, cudaStream_t st) {
-    const RdColumn* c = (const RdColumn*)cols;
-    switch (n) {
-        case 256: return launch_az<A256>(in, out, n_lines, tw, c, r_near, st);
-        case 512: return launch_az<A512>(in, out, n_lines, tw, c, r_near, st);
-        case 1024: return launch_az<A1024>(in, out, n_lines, tw, c, r_near, st);
-        case 2048: return launch_az<A2048>(in, out, n_lines, tw, c, r_near, st);
-        case 4096: return launch_az<A4096>(in, out, n_lines, tw, c, r_near, st);
-        case 8192: return launch_az<A8192>(in, out, n_lines, tw, c, r_near, st);
-        case 16384: return launch_az<A16384>(in, out, n_lines, tw, c, r_near, st);
-    }
-    return cudaErrorInvalidValue;
+    return launch_az_n<true>(n, in, out, n_lines, tw, (const RdColumn*)cols, r_near, st);
+}
+
+// Forward FFT of n_lines lines of n (natural order in and out, in place
+// allowed) with the twiddles of rd_az_schedule(n).
+cudaError_t launch_az_fft_rd(int n, const float2* in, float2* out, int64_t n_lines, const float2* tw,
+                             cudaStream_t st) {
+    return launch_az_n<false>(n, in, out, n_lines, tw, nullptr, 0.0, st);
 }
 
 cudaError_t launch_rcmc(int taps, const float2* in, float2* out, int n_range, int n_f, const void* cols,

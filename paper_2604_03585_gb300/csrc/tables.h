@@ -22,6 +22,7 @@ void mma_filter_positions(int n, int32_t *idx);
 const char *rd_az_schedule(int n);
 cudaError_t launch_az_compress_rd(int n, const float2 *in, float2 *out, int64_t n_lines, const float2 *tw,
                                   const void *cols, double r_near, cudaStream_t st);
+cudaError_t launch_az_fft_rd(int n, const float2 *in, float2 *out, int64_t n_lines, const float2 *tw, cudaStream_t st);
 cudaError_t launch_rcmc(int taps, const float2 *in, float2 *out, int n_range, int n_f, const void *cols,
                         double r_near, int staged_rows, cudaStream_t st);
 int rcmc_staged_rows(int n_range, int n_f, double r_near, const void *host_cols);

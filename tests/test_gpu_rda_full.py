@@ -117,3 +117,22 @@ def test_geometry_refusals(sar):
     with pytest.raises(sar.SarError):
         sar.sar_rcmc(plan, y, y)                                             # overlap
     plan.destroy()
+
+
+@pytest.mark.parametrize("n_az", [256, 512, 1024, 2048, 4096, 8192, 16384])
+def test_full_rda_every_azimuth_length(sar, n_az):
+    """The full processor at every azimuth length its kernels are compiled
+    for (each with its own twiddle tables): one migrating target, 256 range
+    bins, against the oracle."""
+    orc = oracle.default()
+    geo = sarsim.Geometry(10.0, 0.3, 4000.0)
+    tg = [(n_az // 2, 128)]
+    raw = sarsim.echo_migration(n_az, 256, tg, (32, 16.0), min(512, n_az // 2), geo, 20.0, 9)
+    Hr = orc.matched_filter(256, sarsim.lfm_chirp(32, 16.0)).astype(np.complex64)
+    img = run_full(sar, raw, Hr, geo, 16)
+    ref = orc.rda_full(raw, Hr.astype(np.complex128), geo, taps=16, nthreads=NTHREADS)
+    err = M.rel_l2(img, ref)
+    print(f"\nFULL RDA n_az={n_az}: rel_l2 = {err:.3e}")
+    assert err < 2e-5, err
+    (a0, n0), = tg
+    assert M.peak(img, (n0, a0)) == M.peak(ref, (n0, a0))
