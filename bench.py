@@ -564,8 +564,21 @@ def rda_full_bench(sar, dev, stream, work, image, reps: int = 50) -> dict:
             times.append(e0.elapsed_time(e1))
     times.sort()
     ms = times[len(times) // 2]
+    # RCMC alone on the range-Doppler image the azimuth FFT left in `image`
+    # (the input and output, 2 x 134 MB, exceed L2)
+    rc = []
+    for i in range(reps + 3):
+        e0.record(stream)
+        sar.sar_rcmc(plan, image, work, stream)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= 3:
+            rc.append(e0.elapsed_time(e1))
+    rc.sort()
+    rc_ms = rc[len(rc) // 2]
     plan.destroy()
-    return {"ms_per_scene": ms, "kernels_per_scene": 4 if sar.sar_plan_folds_corner_turn else 5,
+    return {"ms_per_scene": ms, "rcmc_ms": rc_ms, "rcmc_GBps": 2 * 8 * N_AZ * N_RANGE / rc_ms / 1e6,
+            "kernels_per_scene": 4 if sar.sar_plan_folds_corner_turn else 5,
             "steps": "range compression + corner turn, azimuth FFT, RCMC (16-tap Hann sinc), "
                      "range-dependent azimuth filter + IFFT",
             "geometry": {"kappa": geo.kappa, "v_s": geo.v_s, "r_near": geo.r_near, "aperture_lines": ap}}

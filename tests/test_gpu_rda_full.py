@@ -74,10 +74,16 @@ def test_full_rda_4096_vs_oracle(sar):
     (1024, 4096, sarsim.Geometry(10.0, 0.3, 4000.0)),   # bins up to 5000: FP32 spacing 5e-4
     (4096, 512, sarsim.Geometry(2.0, 0.3, 100.0)),      # D down to 0.55: shifts up to ~3400 bins
     (256, 1024, sarsim.Geometry(5.0, 0.11, 37.3)),      # fractional r_near, kappa v_s = 0.55
+    (300, 999, sarsim.Geometry(10.0, 0.3, 4000.0)),     # ragged in both: the last tiles partial
+    (256, 512, sarsim.Geometry(3.0, 0.3, 2000.0)),      # ~200 rows per tile: the 128-bin tiles, staged
 ])
 def test_rcmc_vs_oracle(sar, n_range, n_az, geo):
     """RCMC alone on white complex Gaussian range-Doppler data: every
-    interpolation weight shows in the output, element by element."""
+    interpolation weight shows in the output, element by element.  The tiles
+    stage their input rows in shared memory (up to ~200 rows per tile at
+    256 x 512, kappa 3; a partial last tile in both directions at 300 x 999)
+    or, where the migration is too wide for that, read global memory
+    (256 x 1024 at kappa v_s 0.55, 4096 x 512 at kappa 2)."""
     orc = oracle.default()
     rd = sarsim.complex_gaussian(17, 0, n_range * n_az, 1.0).reshape(n_range, n_az)
     ref = orc.rcmc(rd, geo, taps=16)
