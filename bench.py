@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-scenes", type=int, default=16, help="scenes per sar_rda_process_host_n call (e2e)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--range-schedule", default=None, help="schedule of the range pass (default: autotuned)")
     ap.add_argument("--azimuth-schedule", default=None, help="schedule of the azimuth pass (default: autotuned)")
@@ -827,10 +828,31 @@ def main():
         t0 = time.perf_counter()
         sar.sar_rda_process_host(plan, raw_h, img_h, stream)   # returns with the image in host memory
         e2e_calls.append((time.perf_counter() - t0) * 1e3)
-    e2e_ms = allmax(statistics.median(e2e_calls), world)
-    # the copies alone on this machine (pinned, one cudaMemcpyAsync each way): the floor of e2e
+    single_ms = allmax(statistics.median(e2e_calls), world)
+    # a stream of scenes through one call: the echo of scene q + 1 travels in
+    # while the image of scene q travels out (two echoes, the second the first
+    # at half amplitude, and two images, alternating, all pinned; every
+    # scene's copies inside the timed region)
+    SN = max(2, args.e2e_scenes)
+    raw_h2 = (raw_h * 0.5).pin_memory()
+    img_h2 = torch.empty_like(img_h).pin_memory()
+    raws_n = [raw_h if q % 2 == 0 else raw_h2 for q in range(SN)]
+    imgs_n = [img_h if q % 2 == 0 else img_h2 for q in range(SN)]
+    sar.sar_rda_process_host_n(plan, raws_n, imgs_n, stream)
+    barrier(world)
+    stream_calls = []
+    for _ in range(max(3, KE // 4)):
+        t0 = time.perf_counter()
+        sar.sar_rda_process_host_n(plan, raws_n, imgs_n, stream)   # returns with every image in host memory
+        stream_calls.append((time.perf_counter() - t0) * 1e3 / SN)
+    e2e_ms = allmax(statistics.median(stream_calls), world)
+    # the copies alone on this machine (pinned, one cudaMemcpyAsync each way), one
+    # direction at a time (the floor of a single call) and both at once (the
+    # floor of the stream)
     scratch = torch.empty_like(raw_h, device=dev)
-    copy_ms = {"h2d": [], "d2h": []}
+    scratch2 = torch.empty_like(raw_h, device=dev)
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    copy_ms = {"h2d": [], "d2h": [], "both": []}
     for _ in range(5):
         t0 = time.perf_counter()
         scratch.copy_(raw_h, non_blocking=True)
@@ -839,13 +861,24 @@ def main():
         img_h.copy_(scratch, non_blocking=True)
         torch.cuda.synchronize()
         t2 = time.perf_counter()
+        with torch.cuda.stream(s_in):
+            scratch.copy_(raw_h, non_blocking=True)
+        with torch.cuda.stream(s_out):
+            img_h2.copy_(scratch2, non_blocking=True)
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
         copy_ms["h2d"].append((t1 - t0) * 1e3)
         copy_ms["d2h"].append((t2 - t1) * 1e3)
-    del scratch
+        copy_ms["both"].append((t3 - t2) * 1e3)
+    del scratch, scratch2
     floor = statistics.median(copy_ms["h2d"]) + statistics.median(copy_ms["d2h"])
-    e2e_stats = {"mean_ms": statistics.mean(e2e_calls), "min_ms": min(e2e_calls), "max_ms": max(e2e_calls),
-                 "calls": KE, "statistic": "median of per-call host wall times",
-                 "copies_alone_ms": floor,
+    e2e_stats = {"scenes_per_call": SN, "calls": len(stream_calls),
+                 "statistic": "median over calls of host wall time per call / scenes per call",
+                 "copies_both_directions_ms": statistics.median(copy_ms["both"]),
+                 "single_call": {"api": "sar_rda_process_host, one scene per call", "median_ms": single_ms,
+                                 "mean_ms": statistics.mean(e2e_calls), "min_ms": min(e2e_calls),
+                                 "max_ms": max(e2e_calls), "calls": KE,
+                                 "copies_alone_ms": floor},
                  "h2d_GBps": raw_h.numel() * 8 / (statistics.median(copy_ms["h2d"]) * 1e-3) / 1e9,
                  "d2h_GBps": img_h.numel() * 8 / (statistics.median(copy_ms["d2h"]) * 1e-3) / 1e9}
 
@@ -933,7 +966,8 @@ def main():
         "gflops_convention": roofline.rda_flops(N_AZ, N_RANGE) / (ms_step * 1e-3) / 1e9,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": raw_h.numel() * 8,
-                "d2h_bytes_per_step": img_h.numel() * 8, "api": "sar_rda_process_host, pinned host buffers",
+                "d2h_bytes_per_step": img_h.numel() * 8,
+                "api": "sar_rda_process_host_n, pinned host buffers: ms per scene of a stream of scenes",
                 **e2e_stats},
         "gpu_launches": (2 if folded else 3) * K,
         **extras,

@@ -221,12 +221,31 @@ SAR_API sar_status sar_rda_full(sar_plan plan, const void *raw, void *work, void
  * SAR_PLAN_OUT_AZ_MAJOR).  Pinned host memory gives the full
  * copy bandwidth.  The plan allocates its device staging buffers on the first
  * call (2 x n_az x n_range x 8 bytes) and keeps them until destroyed.  On a
- * plan that folds the corner turn the call is a pipeline on two internal
- * streams: the echo arrives in 8 blocks of azimuth lines and each block's
- * range pass starts as soon as it has landed; the azimuth pass runs in 8
- * blocks of range bins, each copied back while the next is computed.  One
- * host-buffer call per plan runs at a time. */
+ * plan that folds the corner turn (image [n_range][n_az], n_az a multiple of
+ * 8 x its cluster or block size, n_range of 8) the call is a pipeline on
+ * internal copy-in, compute and copy-out streams: the echo arrives in 8
+ * blocks of azimuth lines and each block's range pass starts as soon as it
+ * has landed; the azimuth pass runs in 8 blocks of range bins, each copied
+ * back while the next is computed.  One host-buffer call per plan runs at a
+ * time.  A single scene's copies cannot overlap each other (its image needs
+ * all of its echo): sar_rda_process_host_n overlaps those of successive
+ * scenes. */
 SAR_API sar_status sar_rda_process_host(sar_plan plan, const void *raw, void *image, sar_stream stream);
+
+/* n_scenes scenes on host buffers in one call, raws[q] -> images[q], each as
+ * sar_rda_process_host computes it (bit for bit).  On a plan whose
+ * single-scene call is pipelined the scenes share one pipeline with two
+ * device staging sets, scene q in set q mod 2: the echo of scene q + 1 is
+ * copied in while the image of scene q is copied out, both directions of the
+ * host link at once.  The plan then keeps the second staging set (another
+ * 2 x n_az x n_range x 8 bytes) until destroyed.  On other plans the scenes
+ * run one after another.  raws: n_scenes host pointers to complex64
+ * [n_az][n_range] (not modified); images: n_scenes host pointers to complex64
+ * images as for sar_rda_process_host; all non-NULL, no image overlapping
+ * another or an echo.  n_scenes = 0 does nothing.  Returns once every image
+ * is in host memory. */
+SAR_API sar_status sar_rda_process_host_n(sar_plan plan, int32_t n_scenes, const void *const *raws,
+                                          void *const *images, sar_stream stream);
 
 /* Matched-filter helper (Sec. II-B step 3, Sec. V-A's chirp signal model):
  * writes H[k] = conj(FFT_n(c)) to out (device complex64[n]) where c is the

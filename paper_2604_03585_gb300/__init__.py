@@ -40,7 +40,7 @@ EXPORTS = ("sar_plan_create", "sar_plan_destroy", "sar_range_compress", "sar_cor
            "sar_azimuth_compress", "sar_rda_process", "sar_range_compress_oop", "sar_range_compress_ct", "sar_rda_process_oop",
            "sar_range_compress_unfused", "sar_azimuth_compress_unfused", "sar_rda_process_unfused",
            "sar_plan_set_geometry", "sar_rcmc", "sar_rda_full",
-           "sar_rda_process_host", "sar_make_lfm_spectrum", "sar_simulate_echo",
+           "sar_rda_process_host", "sar_rda_process_host_n", "sar_make_lfm_spectrum", "sar_simulate_echo",
            "sar_fft_lines", "sar_fft_lines_static", "sar_transpose", "sar_schedule_count", "sar_schedule_get",
            "sar_set_preferred_schedule", "sar_set_corner_turn_variant", "sar_plan_create_ex", "sar_plan_get_schedules", "sar_plan_folds_corner_turn", "sar_autotune",
            "sar_plan_status", "sar_batch_create", "sar_batch_run", "sar_batch_info",
@@ -109,6 +109,7 @@ _SIGS = {
     "sar_rda_full": [_vp, _vp, _vp, _vp, _vp],
     "sar_rda_process_oop": [_vp, _vp, _vp, _vp, _vp],
     "sar_rda_process_host": [_vp, _vp, _vp, _vp],
+    "sar_rda_process_host_n": [_vp, ctypes.c_int32, _vp, _vp, _vp],
     "sar_make_lfm_spectrum": [_i64, _i64, _dbl, _vp, _vp],
     "sar_simulate_echo": [_i64, _i64, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32, _i64, _dbl, _i64, _dbl, _dbl,
                           ctypes.c_uint64, _vp, _vp],
@@ -338,6 +339,16 @@ def sar_rda_process_oop(plan, raw, work, image, stream=None) -> None:
 
 def sar_rda_process_host(plan, raw_host, image_host, stream=None) -> None:
     _check(_lib.sar_rda_process_host(_h(plan), _ptr(raw_host), _ptr(image_host), _stream(stream)))
+
+
+def sar_rda_process_host_n(plan, raws_host, images_host, stream=None) -> None:
+    """Scenes raws_host[q] -> images_host[q] (host buffers) in one call."""
+    if len(raws_host) != len(images_host):
+        raise ValueError("one image per echo")
+    n = len(raws_host)
+    raws = (ctypes.c_void_p * max(n, 1))(*[_ptr(r) for r in raws_host])
+    imgs = (ctypes.c_void_p * max(n, 1))(*[_ptr(m) for m in images_host])
+    _check(_lib.sar_rda_process_host_n(_h(plan), n, raws, imgs, _stream(stream)))
 
 
 def sar_make_lfm_spectrum(n: int, n_chirp: int, tbp: float, out, stream=None) -> None:

@@ -243,12 +243,16 @@ struct sar_plan_s {
     sar::FusedCtl ctl{};
     void *block = nullptr;  // one device allocation holding every table
     std::mutex host_mu;
-    void *stage_raw = nullptr, *stage_img = nullptr;  // lazily, for the host-buffer entry point
-    // lazily, for the chunked host-buffer pipeline: a copy and a compute stream,
-    // one event per chunk and direction, and start / end events
+    // lazily, for the host-buffer entry points: two staging sets (the second
+    // only for calls of several scenes), each an echo and an image
+    void *stage_raw[2] = {}, *stage_img[2] = {};
+    // lazily, for the chunked host-buffer pipeline: copy-in, compute and
+    // copy-out streams, one event per chunk and direction, start / end events,
+    // and per staging set the events that free its echo and its image
     static constexpr int kHostChunks = 8;
-    cudaStream_t host_copy = nullptr, host_compute = nullptr;
+    cudaStream_t host_copy = nullptr, host_compute = nullptr, host_copy_out = nullptr;
     cudaEvent_t host_ev[2 * kHostChunks + 2] = {};
+    cudaEvent_t host_free[4] = {};
     // full Range-Doppler processing (sar_plan_set_geometry)
     void *rd_cols = nullptr;
     double kappa = 0, vs = 0, r_near = 0;
@@ -560,12 +564,17 @@ sar_status sar_autotune(int64_t n, int64_t n_lines, int32_t reps, int32_t kind, 
 sar_status sar_plan_destroy(sar_plan p) {
     if (!p) return SAR_OK;
     cudaFree(p->block);
-    if (p->stage_raw) cudaFree(p->stage_raw);
-    if (p->stage_img) cudaFree(p->stage_img);
+    for (int b = 0; b < 2; ++b) {
+        if (p->stage_raw[b]) cudaFree(p->stage_raw[b]);
+        if (p->stage_img[b]) cudaFree(p->stage_img[b]);
+    }
     if (p->rd_cols) cudaFree(p->rd_cols);
     if (p->host_copy) cudaStreamDestroy(p->host_copy);
     if (p->host_compute) cudaStreamDestroy(p->host_compute);
+    if (p->host_copy_out) cudaStreamDestroy(p->host_copy_out);
     for (cudaEvent_t e : p->host_ev)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : p->host_free)
         if (e) cudaEventDestroy(e);
     delete p;
     return SAR_OK;
@@ -858,87 +867,146 @@ sar_status sar_rda_full(sar_plan p, const void *raw, void *work, void *image, sa
     return SAR_OK;
 }
 
-// The host-buffer path of a folded plan as a pipeline: the echo arrives in
-// kHostChunks blocks of azimuth lines on a copy stream, and each block's
-// range pass (with the folded corner turn, into its columns of the image)
-// starts on a compute stream as soon as the block has landed; the azimuth
-// pass then runs over kHostChunks blocks of range bins, each copied back while
-// the next is computed.  The copies, one direction at a time, set the pace;
-// the compute hides behind them.  Called with p->host_mu held and the staging
-// buffers allocated.
-static sar_status host_pipeline(sar_plan p, const void *raw, void *image, cudaStream_t s) {
+// The host-buffer path of a folded plan as a pipeline over n scenes: each
+// echo arrives in kHostChunks blocks of azimuth lines on the copy-in stream,
+// and each block's range pass (with the folded corner turn, into its columns
+// of the image) starts on the compute stream as soon as the block has landed;
+// the azimuth pass then runs over kHostChunks blocks of range bins, each
+// copied back on the copy-out stream while the next is computed.  Scene q
+// uses staging set q mod 2, so the echo of scene q + 1 travels to the device
+// while the image of scene q travels back: the link carries both directions
+// at once, and the compute hides behind the copies.  A set is reused once its
+// previous scene's range pass has read the echo and its image has been copied
+// out.  Called with p->host_mu held and the staging sets allocated.
+static sar_status host_pipeline(sar_plan p, int n, const void *const *raws, void *const *images, cudaStream_t s) {
     constexpr int K = sar_plan_s::kHostChunks;
     const SchedDesc &dr = *p->range.sched;
     const int64_t A = p->n_az / K, B = p->n_range / K;
     if (!p->host_copy) {
         SAR_CUDA(cudaStreamCreateWithFlags(&p->host_copy, cudaStreamNonBlocking), "cudaStreamCreate");
         SAR_CUDA(cudaStreamCreateWithFlags(&p->host_compute, cudaStreamNonBlocking), "cudaStreamCreate");
+        SAR_CUDA(cudaStreamCreateWithFlags(&p->host_copy_out, cudaStreamNonBlocking), "cudaStreamCreate");
         for (cudaEvent_t &e : p->host_ev) SAR_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+        for (cudaEvent_t &e : p->host_free)
+            SAR_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
     }
-    cudaStream_t sc = p->host_copy, sk = p->host_compute;
+    cudaStream_t si = p->host_copy, sk = p->host_compute, so = p->host_copy_out;
     cudaEvent_t *ev_in = p->host_ev, *ev_out = p->host_ev + K, ev_start = p->host_ev[2 * K],
                 ev_end = p->host_ev[2 * K + 1];
-    float2 *sraw = (float2 *)p->stage_raw, *simg = (float2 *)p->stage_img;
+    cudaEvent_t *raw_free = p->host_free, *img_free = p->host_free + 2;
     const size_t row_r = sizeof(float2) * (size_t)p->n_range, row_a = sizeof(float2) * (size_t)p->n_az;
     SAR_CUDA(cudaEventRecord(ev_start, s), "cudaEventRecord");
-    SAR_CUDA(cudaStreamWaitEvent(sc, ev_start, 0), "cudaStreamWaitEvent");
+    SAR_CUDA(cudaStreamWaitEvent(si, ev_start, 0), "cudaStreamWaitEvent");
     SAR_CUDA(cudaStreamWaitEvent(sk, ev_start, 0), "cudaStreamWaitEvent");
-    for (int k = 0; k < K; ++k) {
-        SAR_CUDA(cudaMemcpyAsync(sraw + k * A * p->n_range, (const char *)raw + k * A * row_r, A * row_r,
-                                 cudaMemcpyHostToDevice, sc),
-                 "host-to-device copy");
-        SAR_CUDA(cudaEventRecord(ev_in[k], sc), "cudaEventRecord");
-        SAR_CUDA(cudaStreamWaitEvent(sk, ev_in[k], 0), "cudaStreamWaitEvent");
-        cudaError_t e = dr.fused_ct(sraw + k * A * p->n_range, simg + k * A, A, p->n_range, p->n_az, p->range.filt,
-                                    p->range.tw, sk);
-        if (e != cudaSuccess) return cuda_fail(e, "range compression + corner turn launch");
+    SAR_CUDA(cudaStreamWaitEvent(so, ev_start, 0), "cudaStreamWaitEvent");
+    for (int q = 0; q < n; ++q) {
+        const int b = q & 1;
+        float2 *sraw = (float2 *)p->stage_raw[b], *simg = (float2 *)p->stage_img[b];
+        if (q >= 2) {
+            SAR_CUDA(cudaStreamWaitEvent(si, raw_free[b], 0), "cudaStreamWaitEvent");
+            SAR_CUDA(cudaStreamWaitEvent(sk, img_free[b], 0), "cudaStreamWaitEvent");
+        }
+        for (int k = 0; k < K; ++k) {
+            SAR_CUDA(cudaMemcpyAsync(sraw + k * A * p->n_range, (const char *)raws[q] + k * A * row_r, A * row_r,
+                                     cudaMemcpyHostToDevice, si),
+                     "host-to-device copy");
+            SAR_CUDA(cudaEventRecord(ev_in[k], si), "cudaEventRecord");
+            SAR_CUDA(cudaStreamWaitEvent(sk, ev_in[k], 0), "cudaStreamWaitEvent");
+            cudaError_t e = dr.fused_ct(sraw + k * A * p->n_range, simg + k * A, A, p->n_range, p->n_az,
+                                        p->range.filt, p->range.tw, sk);
+            if (e != cudaSuccess) return cuda_fail(e, "range compression + corner turn launch");
+        }
+        SAR_CUDA(cudaEventRecord(raw_free[b], sk), "cudaEventRecord");
+        for (int j = 0; j < K; ++j) {
+            float2 *rows = simg + j * B * p->n_az;
+            sar_status st = run_fused(p, p->az, B, rows, rows, sk, "azimuth compression launch");
+            if (st != SAR_OK) return st;
+            SAR_CUDA(cudaEventRecord(ev_out[j], sk), "cudaEventRecord");
+            SAR_CUDA(cudaStreamWaitEvent(so, ev_out[j], 0), "cudaStreamWaitEvent");
+            SAR_CUDA(cudaMemcpyAsync((char *)images[q] + j * B * row_a, rows, B * row_a, cudaMemcpyDeviceToHost, so),
+                     "device-to-host copy");
+        }
+        SAR_CUDA(cudaEventRecord(img_free[b], so), "cudaEventRecord");
     }
-    for (int j = 0; j < K; ++j) {
-        float2 *rows = simg + j * B * p->n_az;
-        sar_status st = run_fused(p, p->az, B, rows, rows, sk, "azimuth compression launch");
-        if (st != SAR_OK) return st;
-        SAR_CUDA(cudaEventRecord(ev_out[j], sk), "cudaEventRecord");
-        SAR_CUDA(cudaStreamWaitEvent(sc, ev_out[j], 0), "cudaStreamWaitEvent");
-        SAR_CUDA(cudaMemcpyAsync((char *)image + j * B * row_a, rows, B * row_a, cudaMemcpyDeviceToHost, sc),
-                 "device-to-host copy");
-    }
-    SAR_CUDA(cudaEventRecord(ev_end, sc), "cudaEventRecord");
+    SAR_CUDA(cudaEventRecord(ev_end, so), "cudaEventRecord");
     SAR_CUDA(cudaStreamWaitEvent(s, ev_end, 0), "cudaStreamWaitEvent");
+    // the copy-in and compute streams finish before copy-out's last copy;
+    // nothing of this call is left on them
     SAR_CUDA(cudaStreamSynchronize(s), "stream synchronise");
     return SAR_OK;
+}
+
+// Allocates staging sets 0 ... sets - 1 (each an echo and an image).
+static sar_status host_staging(sar_plan p, int sets) {
+    const size_t bytes = sizeof(float2) * (size_t)(p->n_az * p->n_range);
+    for (int b = 0; b < sets; ++b) {
+        if (p->stage_raw[b]) continue;
+        void *r = nullptr, *m = nullptr;
+        if (cudaMalloc(&r, bytes) != cudaSuccess || cudaMalloc(&m, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            if (r) cudaFree(r);
+            return fail(SAR_ERR_OUT_OF_MEMORY, "staging buffers (2 x %zu bytes)", bytes);
+        }
+        p->stage_raw[b] = r;
+        p->stage_img[b] = m;
+    }
+    return SAR_OK;
+}
+
+// One scene through staging set 0 without the pipeline (plans that do not
+// fold the corner turn, azimuth-major output, or block sizes that do not divide).
+static sar_status host_serial(sar_plan p, const void *raw, void *image, cudaStream_t s) {
+    const size_t bytes = sizeof(float2) * (size_t)(p->n_az * p->n_range);
+    SAR_CUDA(cudaMemcpyAsync(p->stage_raw[0], raw, bytes, cudaMemcpyHostToDevice, s), "host-to-device copy");
+    sar_status st = rda3(p, p->stage_raw[0], p->stage_img[0], s);
+    if (st != SAR_OK) return st;
+    const void *result = p->stage_img[0];
+    if (p->az_major) {   // the fourth pass, into the staged raw echo (no longer needed)
+        cudaError_t e = sar::launch_transpose((const float2 *)p->stage_img[0], (float2 *)p->stage_raw[0], p->n_range,
+                                              p->n_az, s);
+        if (e != cudaSuccess) return cuda_fail(e, "transpose back launch");
+        result = p->stage_raw[0];
+    }
+    SAR_CUDA(cudaMemcpyAsync(image, result, bytes, cudaMemcpyDeviceToHost, s), "device-to-host copy");
+    SAR_CUDA(cudaStreamSynchronize(s), "stream synchronise");
+    return SAR_OK;
+}
+
+static bool host_pipelined(const sar_plan_s *p) {
+    constexpr int K = sar_plan_s::kHostChunks;
+    return p->fold && !p->az_major && p->n_az % (K * p->range.sched->ct_lines) == 0 && p->n_range % K == 0;
 }
 
 sar_status sar_rda_process_host(sar_plan p, const void *raw, void *image, sar_stream stream) {
     if (!p) return fail(SAR_ERR_INVALID_ARG, "plan is NULL");
     if (!raw || !image) return fail(SAR_ERR_INVALID_ARG, "raw or image is NULL");
-    const size_t bytes = sizeof(float2) * (size_t)(p->n_az * p->n_range);
     cudaStream_t s = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(p->host_mu);   // one host-buffer call per plan at a time
-    if (!p->stage_raw) {
-        if (cudaMalloc(&p->stage_raw, bytes) != cudaSuccess || cudaMalloc(&p->stage_img, bytes) != cudaSuccess) {
-            cudaGetLastError();
-            if (p->stage_raw) cudaFree(p->stage_raw);
-            p->stage_raw = p->stage_img = nullptr;
-            return fail(SAR_ERR_OUT_OF_MEMORY, "staging buffers (2 x %zu bytes)", bytes);
-        }
+    sar_status st;
+    if ((st = host_staging(p, 1)) != SAR_OK) return st;
+    if (host_pipelined(p)) return host_pipeline(p, 1, &raw, &image, s);
+    return host_serial(p, raw, image, s);
+}
+
+sar_status sar_rda_process_host_n(sar_plan p, int32_t n_scenes, const void *const *raws, void *const *images,
+                                  sar_stream stream) {
+    if (!p) return fail(SAR_ERR_INVALID_ARG, "plan is NULL");
+    if (n_scenes < 0) return fail(SAR_ERR_INVALID_ARG, "n_scenes < 0");
+    if (n_scenes == 0) return SAR_OK;
+    if (!raws || !images) return fail(SAR_ERR_INVALID_ARG, "raws or images is NULL");
+    for (int32_t q = 0; q < n_scenes; ++q)
+        if (!raws[q] || !images[q]) return fail(SAR_ERR_INVALID_ARG, "raws[%d] or images[%d] is NULL", q, q);
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(p->host_mu);
+    sar_status st;
+    if (!host_pipelined(p)) {
+        if ((st = host_staging(p, 1)) != SAR_OK) return st;
+        for (int32_t q = 0; q < n_scenes; ++q)
+            if ((st = host_serial(p, raws[q], images[q], s)) != SAR_OK) return st;
+        return SAR_OK;
     }
-    constexpr int K = sar_plan_s::kHostChunks;
-    const SchedDesc &dr = *p->range.sched;
-    if (p->fold && !p->az_major && p->n_az % (K * dr.ct_lines) == 0 && p->n_range % K == 0)
-        return host_pipeline(p, raw, image, s);
-    SAR_CUDA(cudaMemcpyAsync(p->stage_raw, raw, bytes, cudaMemcpyHostToDevice, s), "host-to-device copy");
-    sar_status st = rda3(p, p->stage_raw, p->stage_img, s);
-    if (st != SAR_OK) return st;
-    const void *result = p->stage_img;
-    if (p->az_major) {   // the fourth pass, into the staged raw echo (no longer needed)
-        cudaError_t e = sar::launch_transpose((const float2 *)p->stage_img, (float2 *)p->stage_raw, p->n_range,
-                                              p->n_az, s);
-        if (e != cudaSuccess) return cuda_fail(e, "transpose back launch");
-        result = p->stage_raw;
-    }
-    SAR_CUDA(cudaMemcpyAsync(image, result, bytes, cudaMemcpyDeviceToHost, s), "device-to-host copy");
-    SAR_CUDA(cudaStreamSynchronize(s), "stream synchronise");
-    return SAR_OK;
+    if ((st = host_staging(p, n_scenes > 1 ? 2 : 1)) != SAR_OK) return st;
+    return host_pipeline(p, n_scenes, raws, images, s);
 }
 
 sar_status sar_fft_lines(int64_t n, int64_t n_lines, const void *in, void *out, int inverse, sar_stream stream) {

@@ -453,6 +453,56 @@ def test_host_entry_point_4096_matches_device(sar, flags):
     plan.destroy()
 
 
+@pytest.mark.parametrize("size,flags", [(256, 0), (4096, 0), (4096, 1)],
+                         ids=["256-pipelined", "4096-pipelined", "4096-unfolded"])
+def test_host_n_scenes_match_device(sar, size, flags):
+    """sar_rda_process_host_n over three different scenes (two device staging
+    sets on folded plans, the sets reused by the third scene) gives each
+    scene's device-buffer image bit for bit, and a second call reuses the
+    pipeline's streams and events."""
+    import dataclasses
+    base = sarsim.scene_256() if size == 256 else sarsim.scene_4096()
+    specs = [dataclasses.replace(base, seed=base.seed + q) for q in range(3)]
+    Hr, Ha = gpu_filters(sar, base)
+    plan = sar.sar_plan_create(base.n_range, base.n_az, Hr, Ha, flags=flags)
+    raws = [sarsim.echo(sp) for sp in specs]
+    want = []
+    for raw in raws:
+        img = empty_c64(base.n_range, base.n_az)
+        sar.sar_rda_process_oop(plan, dev(raw), empty_c64(base.n_az, base.n_range), img)
+        want.append(host(img))
+    assert not np.array_equal(want[0], want[1])
+    raws_h = [torch.from_numpy(r).pin_memory() for r in raws]
+    imgs_h = [torch.empty((base.n_range, base.n_az), dtype=torch.complex64).pin_memory() for _ in raws]
+    for _ in range(2):
+        for m in imgs_h:
+            m.zero_()
+        sar.sar_rda_process_host_n(plan, raws_h, imgs_h)
+        for m, w in zip(imgs_h, want):
+            assert np.array_equal(m.numpy(), w)
+    for r, r_h in zip(raws, raws_h):
+        assert np.array_equal(r_h.numpy(), r)            # host echoes untouched
+    sar.sar_rda_process_host_n(plan, raws_h[:1], imgs_h[:1])   # one scene: the single-call pipeline
+    assert np.array_equal(imgs_h[0].numpy(), want[0])
+    assert sar.sar_plan_folds_corner_turn(plan) == (flags == 0)
+    plan.destroy()
+
+
+def test_host_n_refusals(sar):
+    spec = sarsim.scene_256()
+    Hr, Ha = gpu_filters(sar, spec)
+    plan = sar.sar_plan_create(spec.n_range, spec.n_az, Hr, Ha)
+    raw_h = torch.zeros((spec.n_az, spec.n_range), dtype=torch.complex64).pin_memory()
+    img_h = torch.empty((spec.n_range, spec.n_az), dtype=torch.complex64).pin_memory()
+    sar.sar_rda_process_host_n(plan, [], [])                              # nothing to do
+    with pytest.raises(sar.SarError) as e:
+        sar.sar_rda_process_host_n(plan, [raw_h, 0], [img_h, img_h])      # a NULL echo
+    assert e.value.status == sar.SAR_ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        sar.sar_rda_process_host_n(plan, [raw_h], [img_h, img_h])
+    plan.destroy()
+
+
 def test_guard_bands_untouched(sar):
     n_az, n_r, guard = 256, 512, 4096
     plan = make_plan(sar, n_r, n_az, rand_c64(n_r, 1), rand_c64(n_az, 2))
