@@ -27,6 +27,12 @@ import sys
 import threading
 import time
 
+# 32 hardware work queues instead of 8, set before CUDA starts: the serving
+# section runs one stream per in-flight request and size class, and stream
+# priorities only order work on different queues (with 8, a small request can
+# wait behind a large one queued ahead of it on a shared queue)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -688,9 +694,32 @@ def serving_bench(sar, dev, stream, n_requests: int = 2000, budget_gib: int = 12
                 sar.sar_make_lfm_spectrum(size, *sp.az_chirp, ha, stream)
                 classes.append(dict(n_range=size, n_az=size, pool=pool, range_spectrum=hr, az_spectrum=ha))
     torch.cuda.synchronize()
-    srv = sar.sar_server_create(classes, hbm_budget_bytes=budget_gib << 30, max_inflight=max_inflight)
     draws = sarsim.serving_requests(5, n_requests, variants)
     cls = [k * variants + v for k, v in draws]
+    size_of = [classes[c]["n_range"] for c in cls]
+
+    def loads(srv, sat) -> dict:
+        res_out = {}
+        for load in (0.5, 0.9):
+            arrivals = sarsim.poisson_arrivals(5 + int(load * 10), n_requests, load * sat)
+            res = sar.sar_server_run(srv, [(float(t), c) for t, c in zip(arrivals, cls)],
+                                     mode=sar.SAR_SERVE_OPEN_LOOP)
+            if any(r["status"] != 0 for r in res):
+                raise RuntimeError("a served request failed")
+            lat = np.array([r["latency_s"] for r in res]) * 1e3
+            span = max(r["done_s"] for r in res) - float(arrivals[0])
+            by_size = {f"{n}^2": float(np.percentile([x for x, m in zip(lat, size_of) if m == n], 99))
+                       for n in sarsim.SERVING_SIZES if n in size_of}
+            res_out[f"load_{int(load * 100)}pct"] = {
+                "offered_scenes_per_s": load * sat, "achieved_scenes_per_s": n_requests / span,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "max_ms": float(lat.max()), "p99_ms_by_size": by_size}
+        return res_out
+
+    # the served configuration: smaller scenes on higher-priority streams
+    out_env = {"CUDA_DEVICE_MAX_CONNECTIONS": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS")}
+    srv = sar.sar_server_create(classes, hbm_budget_bytes=budget_gib << 30, max_inflight=max_inflight,
+                                size_priority=True)
     sar.sar_server_run(srv, [(0.0, c) for c in cls[:64]], mode=sar.SAR_SERVE_CLOSED_LOOP)     # warm-up
     res = sar.sar_server_run(srv, [(0.0, c) for c in cls], mode=sar.SAR_SERVE_CLOSED_LOOP)
     makespan = max(r["done_s"] for r in res)
@@ -699,20 +728,16 @@ def serving_bench(sar, dev, stream, n_requests: int = 2000, budget_gib: int = 12
     out = {"requests": n_requests, "size_mix": dict(zip([f"{n}^2" for n in sarsim.SERVING_SIZES],
                                                         sarsim.SERVING_MIX)),
            "hbm_budget_GiB": budget_gib, "max_inflight": max_inflight, "mean_scene_MiB": mean_bytes / 2 ** 20,
+           "size_priority": True, "env": out_env,
            "saturation_scenes_per_s": sat,
            "saturation_latency_ms": {"p50": float(np.percentile([r["latency_s"] for r in res], 50) * 1e3),
                                      "p99": float(np.percentile([r["latency_s"] for r in res], 99) * 1e3)}}
-    for load in (0.5, 0.9):
-        arrivals = sarsim.poisson_arrivals(5 + int(load * 10), n_requests, load * sat)
-        res = sar.sar_server_run(srv, [(float(t), c) for t, c in zip(arrivals, cls)], mode=sar.SAR_SERVE_OPEN_LOOP)
-        if any(r["status"] != 0 for r in res):
-            raise RuntimeError("a served request failed")
-        lat = np.array([r["latency_s"] for r in res]) * 1e3
-        span = max(r["done_s"] for r in res) - float(arrivals[0])
-        out[f"load_{int(load * 100)}pct"] = {"offered_scenes_per_s": load * sat, "achieved_scenes_per_s": n_requests / span,
-                                            "p50_ms": float(np.percentile(lat, 50)),
-                                            "p99_ms": float(np.percentile(lat, 99)),
-                                            "mean_ms": float(lat.mean()), "max_ms": float(lat.max())}
+    out.update(loads(srv, sat))
+    srv.destroy()
+    # the same offered loads with every request at one stream priority
+    srv = sar.sar_server_create(classes, hbm_budget_bytes=budget_gib << 30, max_inflight=max_inflight)
+    sar.sar_server_run(srv, [(0.0, c) for c in cls[:64]], mode=sar.SAR_SERVE_CLOSED_LOOP)
+    out["one_priority"] = loads(srv, sat)
     srv.destroy()
     out["inputs"] = ("pool scenes by the device simulator (sarsim.serving_scene, 2 variants per size), "
                      "requests sarsim.serving_requests(5, n), Poisson arrivals sarsim.poisson_arrivals")

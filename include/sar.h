@@ -374,7 +374,16 @@ SAR_API sar_status sar_batch_destroy(sar_batch batch);
  * optionally copies the image out, frees its buffers and records a completion
  * event.  Requests on different slots overlap on the GPU.  When the oldest
  * waiting request does not fit, later ones that do fit may pass it for at
- * most backfill_s seconds. */
+ * most backfill_s seconds.  With size_priority set, each slot holds one
+ * stream per distinct scene size, and a request runs on the one of its
+ * class.  Stream priority rises as scene size falls, up to the device's
+ * range of priorities.  When SMs free up, the waiting blocks of smaller scenes
+ * are dispatched first.  Admission order and every result are unchanged.
+ * Priorities only order work on different hardware work queues.  A process
+ * that serves with size_priority should therefore set
+ * CUDA_DEVICE_MAX_CONNECTIONS=32 before its first CUDA call.  Under the
+ * default of 8 queues, slots share queues, and a small request can wait behind
+ * a large one queued ahead of it. */
 typedef struct {
     int32_t n_classes;                   /* size classes */
     int32_t max_inflight;                /* concurrent requests, 1 ... 256 */
@@ -385,6 +394,7 @@ typedef struct {
     const void *const *az_spectrum;      /* [n_classes] device complex64[n_az] */
     int64_t hbm_budget_bytes;            /* admission budget */
     double backfill_s;                   /* how long later requests may pass a blocked head */
+    int32_t size_priority;               /* nonzero: smaller scenes on higher-priority streams */
 } sar_server_config;
 
 typedef struct {

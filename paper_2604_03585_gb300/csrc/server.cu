@@ -12,7 +12,13 @@
 // A completion poller releases budget and slots; latency = completion time on
 // the GPU clock - arrival time.  When the oldest waiting request does not fit
 // the remaining budget, later requests that do fit may pass it for at most
-// `backfill_s` seconds, after which admission waits for it.
+// `backfill_s` seconds, after which admission waits for it.  With
+// size_priority, a slot holds one stream per size class and a request runs on
+// the stream of its class, whose CUDA stream priority rises as the class's
+// scene size falls: when SMs free up, the block scheduler dispatches the
+// waiting blocks of smaller scenes first (shortest job first at block
+// granularity; no work is dropped or reordered within a request).
+#include <algorithm>
 #include <chrono>
 #include <deque>
 #include <new>
@@ -29,7 +35,7 @@ sar_status validate_device_ptr(const void *p, const char *what);
 namespace {
 
 struct Slot {
-    cudaStream_t stream = nullptr;
+    std::vector<cudaStream_t> streams;   // one per priority level in use
     cudaEvent_t done = nullptr;
     int req = -1;
     int64_t footprint = 0;
@@ -39,6 +45,7 @@ struct Class {
     int64_t n_range = 0, n_az = 0;
     const void *pool = nullptr;
     sar_plan plan = nullptr;
+    int level = 0;   // index of the slot stream its requests run on
     size_t bytes() const { return (size_t)n_range * (size_t)n_az * 8; }
 };
 
@@ -57,7 +64,8 @@ static void server_free(sar_server s) {
     if (!s) return;
     for (auto &sl : s->slots) {
         if (sl.done) cudaEventDestroy(sl.done);
-        if (sl.stream) cudaStreamDestroy(sl.stream);
+        for (cudaStream_t st : sl.streams)
+            if (st) cudaStreamDestroy(st);
     }
     for (auto &c : s->classes)
         if (c.plan) sar_plan_destroy(c.plan);
@@ -111,9 +119,35 @@ sar_status sar_server_create(const sar_server_config *cfg, sar_server *out) {
         uint64_t keep = ~0ULL;   // keep freed memory in the pool for the next requests
         e = cudaMemPoolSetAttribute(s->mempool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
+    if (e == cudaSuccess) {
+        // no reuse through an inserted wait on another slot's stream: a request
+        // would then wait for the request that freed the memory (with size
+        // priority, often a starved large one).  Budget is released only after
+        // a request's frees have completed, so memory freed by finished
+        // requests is reused without a wait and the pool stays within the budget.
+        int no = 0;
+        e = cudaMemPoolSetAttribute(s->mempool, cudaMemPoolReuseAllowInternalDependencies, &no);
+    }
+    // stream priorities: one level per distinct scene size, the smallest size
+    // at the greatest priority (numerically lowest), clamped to the device's range
+    std::vector<int> prio(1, 0);
+    if (cfg->size_priority) {
+        int least = 0, greatest = 0;
+        if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        std::vector<size_t> sizes;
+        for (const Class &c : s->classes) sizes.push_back(c.bytes());
+        std::sort(sizes.begin(), sizes.end());
+        sizes.erase(std::unique(sizes.begin(), sizes.end()), sizes.end());
+        prio.assign(sizes.size(), 0);
+        for (size_t r = 0; r < sizes.size(); ++r) prio[r] = std::min(greatest + (int)r, least);
+        for (Class &c : s->classes)
+            c.level = (int)(std::lower_bound(sizes.begin(), sizes.end(), c.bytes()) - sizes.begin());
+    }
     s->slots.resize(cfg->max_inflight);
     for (auto &sl : s->slots) {
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+        sl.streams.assign(prio.size(), nullptr);
+        for (size_t r = 0; r < prio.size(); ++r)
+            if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&sl.streams[r], cudaStreamNonBlocking, prio[r]);
         if (e == cudaSuccess) e = cudaEventCreate(&sl.done);
     }
     if (e == cudaSuccess) e = cudaEventCreate(&s->base);
@@ -139,7 +173,7 @@ sar_status sar_server_run(sar_server s, const sar_request *reqs, int32_t n, int3
     }
     using clock = std::chrono::steady_clock;
     if (cudaDeviceSynchronize() != cudaSuccess) return sar::report_error(SAR_ERR_CUDA, "device not idle");
-    cudaEventRecord(s->base, s->slots[0].stream);
+    cudaEventRecord(s->base, s->slots[0].streams[0]);
     cudaEventSynchronize(s->base);
     const auto t0 = clock::now();
     auto now_s = [&]() { return std::chrono::duration<double>(clock::now() - t0).count(); };
@@ -153,20 +187,21 @@ sar_status sar_server_run(sar_server s, const sar_request *reqs, int32_t n, int3
     auto admit = [&](int i, Slot &sl) -> bool {
         const Class &c = s->classes[reqs[i].size_class];
         const size_t bytes = c.bytes();
+        cudaStream_t st = sl.streams[c.level];
         void *raw = nullptr, *img = nullptr;
-        if (cudaMallocFromPoolAsync(&raw, bytes, s->mempool, sl.stream) != cudaSuccess ||
-            cudaMallocFromPoolAsync(&img, bytes, s->mempool, sl.stream) != cudaSuccess) {
+        if (cudaMallocFromPoolAsync(&raw, bytes, s->mempool, st) != cudaSuccess ||
+            cudaMallocFromPoolAsync(&img, bytes, s->mempool, st) != cudaSuccess) {
             cudaGetLastError();
             return false;
         }
         res[i].admit_s = now_s();
-        bool ok = cudaMemcpyAsync(raw, c.pool, bytes, cudaMemcpyDeviceToDevice, sl.stream) == cudaSuccess;
-        ok = ok && sar_rda_process(c.plan, raw, img, sl.stream) == SAR_OK;
+        bool ok = cudaMemcpyAsync(raw, c.pool, bytes, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
+        ok = ok && sar_rda_process(c.plan, raw, img, st) == SAR_OK;
         if (ok && reqs[i].output)
-            ok = cudaMemcpyAsync(reqs[i].output, img, bytes, cudaMemcpyDeviceToDevice, sl.stream) == cudaSuccess;
-        cudaFreeAsync(raw, sl.stream);
-        cudaFreeAsync(img, sl.stream);
-        ok = ok && cudaEventRecord(sl.done, sl.stream) == cudaSuccess;
+            ok = cudaMemcpyAsync(reqs[i].output, img, bytes, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
+        cudaFreeAsync(raw, st);
+        cudaFreeAsync(img, st);
+        ok = ok && cudaEventRecord(sl.done, st) == cudaSuccess;
         sl.req = i;
         sl.footprint = (int64_t)(2 * bytes);
         used += sl.footprint;

@@ -39,10 +39,13 @@ def _outputs(classes, sizes):
                        device="cuda") for k in sizes]
 
 
-def test_results_are_the_same_alone_and_in_the_mix(sar, classes):
+@pytest.mark.parametrize("size_priority", [False, True], ids=["one-priority", "size-priority"])
+def test_results_are_the_same_alone_and_in_the_mix(sar, classes, size_priority):
+    """With one stream priority, and with smaller scenes on higher-priority
+    streams (which only changes the order blocks reach the SMs)."""
     rng = sarsim.uniform(21, 3, 0, 48)
     sizes = [int(u * 3) for u in rng]
-    srv = sar.sar_server_create(classes, hbm_budget_bytes=1 << 30, max_inflight=8)
+    srv = sar.sar_server_create(classes, hbm_budget_bytes=1 << 30, max_inflight=8, size_priority=size_priority)
     outs = _outputs(classes, sizes)
     res = sar.sar_server_run(srv, [(0.0, k, o) for k, o in zip(sizes, outs)], mode=sar.SAR_SERVE_CLOSED_LOOP)
     assert all(r["status"] == 0 for r in res)
