@@ -877,8 +877,21 @@ sar_status sar_rda_full(sar_plan p, const void *raw, void *work, void *image, sa
 // while the image of scene q travels back: the link carries both directions
 // at once, and the compute hides behind the copies.  A set is reused once its
 // previous scene's range pass has read the echo and its image has been copied
-// out.  Called with p->host_mu held and the staging sets allocated.
+// out.  Called with p->host_mu held and the staging sets allocated; on an
+// error it returns once the internal streams are idle (no copy is left in
+// flight from or to the caller's host buffers).
+static sar_status host_pipeline_issue(sar_plan p, int n, const void *const *raws, void *const *images,
+                                      cudaStream_t s);
 static sar_status host_pipeline(sar_plan p, int n, const void *const *raws, void *const *images, cudaStream_t s) {
+    const sar_status st = host_pipeline_issue(p, n, raws, images, s);
+    if (st != SAR_OK)
+        for (cudaStream_t q : {p->host_copy, p->host_compute, p->host_copy_out})
+            if (q) cudaStreamSynchronize(q);
+    return st;
+}
+
+static sar_status host_pipeline_issue(sar_plan p, int n, const void *const *raws, void *const *images,
+                                      cudaStream_t s) {
     constexpr int K = sar_plan_s::kHostChunks;
     const SchedDesc &dr = *p->range.sched;
     const int64_t A = p->n_az / K, B = p->n_range / K;
