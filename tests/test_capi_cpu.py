@@ -63,6 +63,10 @@ def test_argument_errors_without_gpu(sar):
     for fn in ("sar_range_compress", "sar_azimuth_compress"):
         assert getattr(lib, fn)(None, None, None) == sar.SAR_ERR_INVALID_ARG
     assert lib.sar_rda_process(None, None, None, None) == sar.SAR_ERR_INVALID_ARG
+    assert lib.sar_rda_process_host(None, None, None, None) == sar.SAR_ERR_INVALID_ARG
+    assert lib.sar_rda_process_host_n(None, 2, None, None, None) == sar.SAR_ERR_INVALID_ARG
+    assert lib.sar_server_create(None, None) == sar.SAR_ERR_INVALID_ARG
+    assert lib.sar_server_destroy(None) == sar.SAR_OK
     assert lib.sar_plan_destroy(None) == sar.SAR_OK
     assert "sm_103a" in sar.sar_version()
 
