@@ -383,7 +383,9 @@ SAR_API sar_status sar_batch_destroy(sar_batch batch);
  * that serves with size_priority should therefore set
  * CUDA_DEVICE_MAX_CONNECTIONS=32 before its first CUDA call.  Under the
  * default of 8 queues, slots share queues, and a small request can wait behind
- * a large one queued ahead of it. */
+ * a large one queued ahead of it.  The largest class gets the SMs no sooner than
+ * the others leave them free.  At high load its latency therefore grows, and
+ * under sustained overload it can be starved; with one priority it cannot. */
 typedef struct {
     int32_t n_classes;                   /* size classes */
     int32_t max_inflight;                /* concurrent requests, 1 ... 256 */
