@@ -385,7 +385,10 @@ SAR_API sar_status sar_batch_destroy(sar_batch batch);
  * default of 8 queues, slots share queues, and a small request can wait behind
  * a large one queued ahead of it.  The largest class gets the SMs no sooner than
  * the others leave them free.  At high load its latency therefore grows, and
- * under sustained overload it can be starved; with one priority it cannot. */
+ * under sustained overload it can be starved; with one priority it cannot.
+ * aging_s > 0 bounds this.  While some request has been in flight for more
+ * than aging_s seconds, only requests of its size or larger are admitted, and
+ * the smaller ones wait in the queue until it completes. */
 typedef struct {
     int32_t n_classes;                   /* size classes */
     int32_t max_inflight;                /* concurrent requests, 1 ... 256 */
@@ -397,6 +400,7 @@ typedef struct {
     int64_t hbm_budget_bytes;            /* admission budget */
     double backfill_s;                   /* how long later requests may pass a blocked head */
     int32_t size_priority;               /* nonzero: smaller scenes on higher-priority streams */
+    double aging_s;                      /* > 0: bound on starvation under size_priority (below) */
 } sar_server_config;
 
 typedef struct {

@@ -74,7 +74,7 @@ class sar_server_config(ctypes.Structure):
                 ("n_range", ctypes.POINTER(ctypes.c_int64)), ("n_az", ctypes.POINTER(ctypes.c_int64)),
                 ("pool", ctypes.POINTER(ctypes.c_void_p)), ("range_spectrum", ctypes.POINTER(ctypes.c_void_p)),
                 ("az_spectrum", ctypes.POINTER(ctypes.c_void_p)), ("hbm_budget_bytes", ctypes.c_int64),
-                ("backfill_s", ctypes.c_double), ("size_priority", ctypes.c_int32)]
+                ("backfill_s", ctypes.c_double), ("size_priority", ctypes.c_int32), ("aging_s", ctypes.c_double)]
 
 
 class sar_request(ctypes.Structure):
@@ -450,7 +450,7 @@ class Server:
 
 
 def sar_server_create(classes, hbm_budget_bytes: int, max_inflight: int = 16, backfill_s: float = 0.05,
-                      size_priority: bool = False) -> Server:
+                      size_priority: bool = False, aging_s: float = 0.0) -> Server:
     """classes: sequence of dicts with n_range, n_az, pool, range_spectrum, az_spectrum."""
     k = len(classes)
     nr = (ctypes.c_int64 * k)(*[c["n_range"] for c in classes])
@@ -459,7 +459,7 @@ def sar_server_create(classes, hbm_budget_bytes: int, max_inflight: int = 16, ba
     hr = (ctypes.c_void_p * k)(*[_ptr(c["range_spectrum"]) for c in classes])
     ha = (ctypes.c_void_p * k)(*[_ptr(c["az_spectrum"]) for c in classes])
     cfg = sar_server_config(k, max_inflight, nr, na, pool, hr, ha, int(hbm_budget_bytes), float(backfill_s),
-                            1 if size_priority else 0)
+                            1 if size_priority else 0, float(aging_s))
     h = _vp()
     _check(_lib.sar_server_create(ctypes.byref(cfg), ctypes.byref(h)))
     return Server(h.value, (nr, na, pool, hr, ha, cfg, classes))

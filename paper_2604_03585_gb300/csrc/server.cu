@@ -39,6 +39,8 @@ struct Slot {
     cudaEvent_t done = nullptr;
     int req = -1;
     int64_t footprint = 0;
+    double admit_t = 0;   // host time of the request's admission
+    int level = 0;        // its class's priority level
 };
 
 struct Class {
@@ -57,6 +59,7 @@ struct sar_server_s {
     cudaMemPool_t mempool = nullptr;
     int64_t budget = 0;
     double backfill_s = 0.05;
+    double aging_s = 0;   // 0: no aging
     cudaEvent_t base = nullptr;
 };
 
@@ -89,6 +92,7 @@ sar_status sar_server_create(const sar_server_config *cfg, sar_server *out) {
     if (!s) return sar::report_error(SAR_ERR_OUT_OF_MEMORY, "host allocation failed");
     s->budget = cfg->hbm_budget_bytes;
     s->backfill_s = cfg->backfill_s > 0 ? cfg->backfill_s : 0.0;
+    s->aging_s = cfg->aging_s > 0 ? cfg->aging_s : 0.0;
     sar_status st = SAR_OK;
     for (int32_t k = 0; k < cfg->n_classes && st == SAR_OK; ++k) {
         Class c;
@@ -203,6 +207,8 @@ sar_status sar_server_run(sar_server s, const sar_request *reqs, int32_t n, int3
         cudaFreeAsync(img, st);
         ok = ok && cudaEventRecord(sl.done, st) == cudaSuccess;
         sl.req = i;
+        sl.admit_t = res[i].admit_s;
+        sl.level = c.level;
         sl.footprint = (int64_t)(2 * bytes);
         used += sl.footprint;
         res[i].status = ok ? SAR_OK : SAR_ERR_CUDA;
@@ -228,13 +234,25 @@ sar_status sar_server_run(sar_server s, const sar_request *reqs, int32_t n, int3
             ++done;
             progress = true;
         }
-        // admissions: oldest first; later ones may pass a head that does not
-        // fit for at most backfill_s
+        // aging: while a request has been in flight longer than aging_s, only
+        // requests of its priority level or lower (its size or larger) are
+        // admitted, so the work already queued ahead of it drains and its
+        // blocks reach the SMs
+        int floor_level = 0;
+        if (s->aging_s > 0)
+            for (const auto &sl : s->slots)
+                if (sl.req >= 0 && t - sl.admit_t > s->aging_s) floor_level = std::max(floor_level, sl.level);
+        auto eligible = [&](int j) { return s->classes[reqs[j].size_class].level >= floor_level; };
+        // admissions: oldest eligible first; later ones may pass a head that
+        // does not fit for at most backfill_s
         for (auto &sl : s->slots) {
             if (sl.req >= 0 || queue.empty()) continue;
+            size_t h = 0;
+            while (h < queue.size() && h < 256 && !eligible(queue[h])) ++h;
+            if (h == queue.size() || h == 256) break;
             int pick = -1;
-            size_t pos = 0;
-            const int head = queue.front();
+            size_t pos = h;
+            const int head = queue[h];
             const int64_t head_fp = 2 * (int64_t)s->classes[reqs[head].size_class].bytes();
             if (used + head_fp <= s->budget) {
                 pick = head;
@@ -242,9 +260,9 @@ sar_status sar_server_run(sar_server s, const sar_request *reqs, int32_t n, int3
             } else {
                 if (head_blocked_since < 0) head_blocked_since = t;
                 if (t - head_blocked_since <= s->backfill_s) {
-                    for (size_t k = 1; k < queue.size() && k < 256; ++k) {
+                    for (size_t k = h + 1; k < queue.size() && k < 256; ++k) {
                         const int j = queue[k];
-                        if (used + 2 * (int64_t)s->classes[reqs[j].size_class].bytes() <= s->budget) {
+                        if (eligible(j) && used + 2 * (int64_t)s->classes[reqs[j].size_class].bytes() <= s->budget) {
                             pick = j;
                             pos = k;
                             break;

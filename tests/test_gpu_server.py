@@ -39,13 +39,17 @@ def _outputs(classes, sizes):
                        device="cuda") for k in sizes]
 
 
-@pytest.mark.parametrize("size_priority", [False, True], ids=["one-priority", "size-priority"])
-def test_results_are_the_same_alone_and_in_the_mix(sar, classes, size_priority):
-    """With one stream priority, and with smaller scenes on higher-priority
-    streams (which only changes the order blocks reach the SMs)."""
+@pytest.mark.parametrize("size_priority,aging_s", [(False, 0.0), (True, 0.0), (True, 1e-6)],
+                         ids=["one-priority", "size-priority", "size-priority-aging"])
+def test_results_are_the_same_alone_and_in_the_mix(sar, classes, size_priority, aging_s):
+    """With one stream priority, with smaller scenes on higher-priority
+    streams (which only changes the order blocks reach the SMs), and with
+    aging so short that admission is restricted most of the time (which only
+    changes the admission order)."""
     rng = sarsim.uniform(21, 3, 0, 48)
     sizes = [int(u * 3) for u in rng]
-    srv = sar.sar_server_create(classes, hbm_budget_bytes=1 << 30, max_inflight=8, size_priority=size_priority)
+    srv = sar.sar_server_create(classes, hbm_budget_bytes=1 << 30, max_inflight=8, size_priority=size_priority,
+                                aging_s=aging_s)
     outs = _outputs(classes, sizes)
     res = sar.sar_server_run(srv, [(0.0, k, o) for k, o in zip(sizes, outs)], mode=sar.SAR_SERVE_CLOSED_LOOP)
     assert all(r["status"] == 0 for r in res)
