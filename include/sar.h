@@ -241,9 +241,10 @@ SAR_API sar_status sar_rda_process_host(sar_plan plan, const void *raw, void *im
  * 2 x n_az x n_range x 8 bytes) until destroyed.  On other plans the scenes
  * run one after another.  raws: n_scenes host pointers to complex64
  * [n_az][n_range] (not modified); images: n_scenes host pointers to complex64
- * images as for sar_rda_process_host; all non-NULL, no image overlapping
- * another or an echo.  n_scenes = 0 does nothing.  Returns once every image
- * is in host memory. */
+ * images as for sar_rda_process_host; all non-NULL.  An image may not overlap
+ * any echo (SAR_ERR_INVALID_ARG).  One image buffer may serve several scenes:
+ * images are written in scene order, so it ends up holding the last of them.
+ * n_scenes = 0 does nothing.  Returns once every image is in host memory. */
 SAR_API sar_status sar_rda_process_host_n(sar_plan plan, int32_t n_scenes, const void *const *raws,
                                           void *const *images, sar_stream stream);
 

@@ -1009,6 +1009,12 @@ sar_status sar_rda_process_host_n(sar_plan p, int32_t n_scenes, const void *cons
     if (!raws || !images) return fail(SAR_ERR_INVALID_ARG, "raws or images is NULL");
     for (int32_t q = 0; q < n_scenes; ++q)
         if (!raws[q] || !images[q]) return fail(SAR_ERR_INVALID_ARG, "raws[%d] or images[%d] is NULL", q, q);
+    // an image copied out while a later echo is copied in must not share its memory
+    const size_t bytes = sizeof(float2) * (size_t)(p->n_az * p->n_range);
+    for (int32_t a = 0; a < n_scenes; ++a)
+        for (int32_t b = 0; b < n_scenes; ++b)
+            if (overlaps(images[a], raws[b], bytes))
+                return fail(SAR_ERR_INVALID_ARG, "images[%d] overlaps raws[%d]", a, b);
     cudaStream_t s = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(p->host_mu);
     sar_status st;

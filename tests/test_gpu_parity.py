@@ -500,6 +500,13 @@ def test_host_n_refusals(sar):
     assert e.value.status == sar.SAR_ERR_INVALID_ARG
     with pytest.raises(ValueError):
         sar.sar_rda_process_host_n(plan, [raw_h], [img_h, img_h])
+    with pytest.raises(sar.SarError) as e:
+        sar.sar_rda_process_host_n(plan, [raw_h, raw_h], [img_h, raw_h])   # an image over an echo
+    assert e.value.status == sar.SAR_ERR_INVALID_ARG
+    sar.sar_rda_process_host_n(plan, [raw_h, raw_h, raw_h], [img_h, img_h, img_h])   # one image buffer, three scenes
+    ref = torch.empty_like(img_h).pin_memory()
+    sar.sar_rda_process_host(plan, raw_h, ref)
+    assert torch.equal(img_h, ref)
     plan.destroy()
 
 
