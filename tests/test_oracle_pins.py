@@ -240,20 +240,21 @@ def pin_rcmc_bandlimited_shift(o):
     frequency), and the zero-Doppler column (no migration) must come out
     unchanged up to the rounding of sin(pi t) at integers."""
     geo = GEO_PIN
-    n_range, n_f = 256, 64
-    j = np.arange(n_f)
-    f = np.where(j < n_f // 2, j, j - n_f) / n_f
-    D = np.sqrt(1 - (f / (geo.kappa * geo.v_s)) ** 2)
+    n_range = 256
     n = np.arange(n_range)[:, None]
-    for nu, tol in ((0.05, 1e-3), (-0.2, 2e-3), (0.3, 5e-3)):
-        rd = np.exp(2j * np.pi * nu * n) * np.ones((1, n_f))
-        out = o.rcmc(rd, geo, taps=16)
-        src = n + (geo.r_near + n) * (1.0 / D[None, :] - 1.0)
-        exact = np.exp(2j * np.pi * nu * src)
-        inside = (src >= 10) & (src < n_range - 10)
-        assert np.max(np.abs(out - exact)[inside]) < tol, nu
-        assert np.max(np.abs(out[:, 0] - rd[:, 0])) < 1e-14
-    assert np.max(src - n) > 5.0          # the migration spans several range cells
+    for n_f in (64, 63):   # an odd width: bins j >= (n_f - 1) / 2 + 1 are negative frequencies
+        j = np.arange(n_f)
+        f = np.where(j < n_f // 2, j, j - n_f) / n_f
+        D = np.sqrt(1 - (f / (geo.kappa * geo.v_s)) ** 2)
+        for nu, tol in ((0.05, 1e-3), (-0.2, 2e-3), (0.3, 5e-3)):
+            rd = np.exp(2j * np.pi * nu * n) * np.ones((1, n_f))
+            out = o.rcmc(rd, geo, taps=16)
+            src = n + (geo.r_near + n) * (1.0 / D[None, :] - 1.0)
+            exact = np.exp(2j * np.pi * nu * src)
+            inside = (src >= 10) & (src < n_range - 10)
+            assert np.max(np.abs(out - exact)[inside]) < tol, (n_f, nu)
+            assert np.max(np.abs(out[:, 0] - rd[:, 0])) < 1e-14
+        assert np.max(src - n) > 5.0      # the migration spans several range cells
 
 
 def pin_rda_full_point_target(o):
