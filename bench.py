@@ -452,7 +452,7 @@ def precision_bench(sar, Hr, Ha, raw, work, image, stream, reps: int = 50) -> di
     """Time the 4096^2 scene with each split-precision plan (three kernels:
     range pass, corner turn, azimuth pass) and the FP32 plan through the same
     unfolded path; the images are compared with the FP32 image here and with
-    the FP64 oracle in tests/test_gpu_parity.py (summarised in profiles/)."""
+    the FP64 oracle in tests/test_gpu_parity.py."""
     import torch
     out = {}
     ref = None
@@ -475,8 +475,8 @@ def precision_bench(sar, Hr, Ha, raw, work, image, stream, reps: int = 50) -> di
         diff = float(torch.linalg.vector_norm(img - ref) / torch.linalg.vector_norm(ref))
         out[name] = {"ms_per_scene": times[len(times) // 2], "rel_l2_vs_fp32_path": diff}
         plan.destroy()
-    out["note"] = ("unfolded three-kernel path for every precision; error against the FP64 oracle: "
-                   "profiles/precision_4096.md")
+    out["note"] = ("unfolded three-kernel path for every precision; the error against the FP64 oracle "
+                   "is checked by the parity tests")
     return out
 
 

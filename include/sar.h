@@ -300,8 +300,10 @@ SAR_API sar_status sar_fft_lines(int64_t n, int64_t n_lines, const void *in, voi
  * call rewrites that array on its stream before its FFT, and all calls share
  * it: calls that may run at the same time on the GPU (different streams with
  * no ordering between them) race on it, so order them.  The first call on a
- * device looks up the array's address once; make it before any stream
- * capture. */
+ * device looks up the array's address once, and the first call at each line
+ * length loads that length's kernels (CUDA loads modules lazily by default)
+ * and sets their attributes once: make one call per line length on each
+ * device before any stream capture. */
 SAR_API sar_status sar_fft_lines_static(int64_t n, int64_t n_lines, const void *in, void *out, int inverse,
                                         sar_stream stream);
 

@@ -10,9 +10,10 @@
 // start-up and forbid any later allocation, and applications whose device
 // memory belongs to a pool allocator that a hidden cudaMalloc could fail
 // against or fragment.  This entry point serves them: its twiddle table lives
-// in a fixed file-scope device array that the CUDA module provides when the
-// library is loaded, and it calls no cudaMalloc, cudaFree or allocating
-// library routine.
+// in a fixed file-scope device array that exists once the CUDA module holding
+// it is loaded (with CUDA's lazy module loading, the default, that happens on
+// first use, not when the library is opened), and it calls no cudaMalloc,
+// cudaFree or allocating library routine.
 //
 // Limits and sharing rules:
 //   * the array holds kStaticTwiddleElems = 32768 complex64 values (256 KiB);
@@ -27,8 +28,10 @@
 //     event between them) race on it and may compute with the wrong table.
 //     Order such calls on one stream, or with events.
 //   * the first call on each device looks up the array's device address once
-//     (cudaGetSymbolAddress) with that device current, and sets the kernels'
-//     shared-memory limits; make that first call before any stream capture.
+//     (cudaGetSymbolAddress) with that device current; the first call at each
+//     line length on a device loads that length's kernels (lazy loading) and
+//     sets their shared-memory limits, once.  Make one call per line length
+//     on each device before any stream capture.
 #include <mutex>
 
 #include "../../include/sar.h"
@@ -50,6 +53,10 @@ __device__ __align__(256) float2 g_static_twiddles[kStaticTwiddleElems];
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 float2 *g_twiddle_addr[kMaxDevices] = {};   // device address of the array, per device
+// schedules whose kernel attributes are set, per device (a schedule is one
+// compiled kernel set: its descriptor's address identifies it)
+constexpr int kMaxPrepared = 64;
+const sar::SchedDesc *g_prepared[kMaxDevices][kMaxPrepared] = {};
 
 // Once per device, with that device current: find where the array lives in
 // this device's memory (the host-side name g_static_twiddles is only a
@@ -69,8 +76,19 @@ sar_status static_twiddles(const sar::SchedDesc &d, float2 **out) {
         }
         g_twiddle_addr[dev] = (float2 *)p;
     }
-    e = d.prepare();   // shared-memory limit of the kernels (an attribute, not an allocation)
-    if (e != cudaSuccess) return sar::report_error(SAR_ERR_CUDA, "cudaFuncSetAttribute failed");
+    // shared-memory limit of the kernels (an attribute, not an allocation),
+    // once per device and schedule
+    bool done = false;
+    int slot = -1;
+    for (int i = 0; i < kMaxPrepared && !done; ++i) {
+        if (g_prepared[dev][i] == &d) done = true;
+        else if (!g_prepared[dev][i] && slot < 0) slot = i;
+    }
+    if (!done) {
+        e = d.prepare();
+        if (e != cudaSuccess) return sar::report_error(SAR_ERR_CUDA, "cudaFuncSetAttribute failed");
+        if (slot >= 0) g_prepared[dev][slot] = &d;
+    }
     *out = g_twiddle_addr[dev];
     return SAR_OK;
 }

@@ -14,6 +14,19 @@
 // `wait_cycles` SM clocks the block records SAR status 5 (timeout) in
 // *status, waits (bounded again) for any copy of its own still in flight,
 // and returns.  No wait can hang the GPU.
+//
+// Why that exit is safe: a block must not end while a bulk copy it started
+// can still write its shared memory.  Every copy this kernel starts reads a
+// whole line that lies inside `in` (line < n_lines, 16-byte aligned, a
+// multiple of 16 bytes) into this block's own shared memory, and its
+// expect_tx byte count equals the copy's size.  Such a copy depends on no
+// other block, thread or event: once issued it completes after one trip
+// through the memory system (microseconds, against a bound of about a
+// second).  A wait can therefore run out only on a copy that was never
+// started (the injected fault below; `pending` stays false for it), and the
+// exit's bounded wait on the copies that were started ends by their
+// completion, never by its bound.  The block leaves through that path only
+// after the pending copies' barriers have completed.
 #pragma once
 
 #include "line_engine.cuh"

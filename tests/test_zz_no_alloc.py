@@ -55,6 +55,33 @@ def test_static_fft_matches_allocating_fft_twice(sar):
         assert rel_l2(got.cpu().numpy(), ref.cpu().numpy()) <= FFT_TOL, call
 
 
+@pytest.mark.parametrize("inverse", [0, 1])
+@pytest.mark.parametrize("n", [256, 512, 1024, 2048, 4096, 8192, 16384])
+def test_static_fft_every_length(sar, n, inverse):
+    """Every power-of-two length the shared array is sized for (16384 needs
+    the largest table, 17,408 values), out of place and in place (in == out),
+    against the allocating entry point."""
+    lib = sar.library()
+    stream = torch.cuda.current_stream().cuda_stream
+    n_lines = 5
+    x = torch.from_numpy(sarsim.complex_gaussian(60 + inverse, n, n * n_lines, 1.0).reshape(n_lines, n)).cuda()
+    ref = torch.empty_like(x)
+    got = torch.empty_like(x)
+    assert lib.sar_fft_lines(n, n_lines, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(ref.data_ptr()),
+                             inverse, ctypes.c_void_p(stream)) == sar.SAR_OK
+    st = lib.sar_fft_lines_static(n, n_lines, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(got.data_ptr()),
+                                  inverse, ctypes.c_void_p(stream))
+    assert st == sar.SAR_OK, sar.sar_last_error()
+    inplace = x.clone()
+    st = lib.sar_fft_lines_static(n, n_lines, ctypes.c_void_p(inplace.data_ptr()),
+                                  ctypes.c_void_p(inplace.data_ptr()), inverse, ctypes.c_void_p(stream))
+    assert st == sar.SAR_OK, sar.sar_last_error()
+    torch.cuda.synchronize()
+    r = ref.cpu().numpy()
+    assert rel_l2(got.cpu().numpy(), r) <= FFT_TOL
+    assert rel_l2(inplace.cpu().numpy(), r) <= FFT_TOL
+
+
 def test_static_fft_refuses_unsupported_sizes(sar):
     lib = sar.library()
     assert lib.sar_fft_lines_static(32768, 1, None, None, 0, None) == sar.SAR_ERR_UNSUPPORTED
