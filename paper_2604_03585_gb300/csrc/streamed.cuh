@@ -297,10 +297,15 @@ __device__ __forceinline__ void fused_range_ct_cluster_body(const float2* in, fl
     }
     static_assert(QC == 4 || QC == 8 || QC == 16, "clusters of 4, 8 or 16 lines");
     constexpr int NQ = SC::N / QC;   // range bins owned by one block
-    static_assert(SC::SMEM_ELEMS >= SC::N, "the receive buffer is one line");
+    // receive row of each line, padded by 4 slots: in the transposed read
+    // below a half-warp reads bins j = 0..7 of rows 2p and 2p + 1 (p = 0, 1);
+    // with rows 2 * RS = 8 (mod 16) bank pairs apart they hit 16 distinct
+    // bank pairs (unpadded rows NQ apart put p = 0 and p = 1 on the same ones)
+    constexpr int RS = NQ + 4;
+    static_assert(QC * RS <= SC::SMEM_ELEMS, "the receive rows fit the line buffer");
     cluster.sync();
     // push: natural-order sample i = lo + r S1 of line a0 + rank goes to
-    // block i / NQ, slot rank NQ + i mod NQ
+    // block i / NQ, slot rank RS + i mod NQ
 #pragma unroll
     for (int s = 0; s < G1; ++s) {
         const int lo = t + SC::T * s;
@@ -308,7 +313,7 @@ __device__ __forceinline__ void fused_range_ct_cluster_body(const float2* in, fl
         for (int r = 0; r < R1; ++r) {
             const int i = lo + r * S1;
             float2* dst = cluster.map_shared_rank(sm, i / NQ);
-            dst[rank * NQ + i % NQ] = v[s * R1 + r];
+            dst[rank * RS + i % NQ] = v[s * R1 + r];
         }
     }
     cluster.sync();
@@ -316,7 +321,7 @@ __device__ __forceinline__ void fused_range_ct_cluster_body(const float2* in, fl
 #pragma unroll 4
     for (int idx = t; idx < NQ * LPN; idx += SC::T) {
         const int j = idx / LPN, p = idx % LPN;
-        const float2 c0 = sm[(2 * p) * NQ + j], c1 = sm[(2 * p + 1) * NQ + j];
+        const float2 c0 = sm[(2 * p) * RS + j], c1 = sm[(2 * p + 1) * RS + j];
         __stcs(reinterpret_cast<float4*>(img + (int64_t)(rank * NQ + j) * ld_img + a0 + 2 * p),
                make_float4(c0.x, c0.y, c1.x, c1.y));
     }
