@@ -339,13 +339,24 @@ typedef struct {
     int32_t azimuth_classes; /* distinct (L, azimuth spectrum) */
 } sar_batch_info_t;
 
-/* Group the strips into classes (a class shares a kernel schedule -- the
- * preferred one of its length -- and a filter), build each class's filter
- * and twiddle tables and segment table, allocate the work buffer
- * (8 bytes per raw sample) and capture the whole batch into one CUDA graph.
+/* Group the strips into classes (a class shares a line geometry and a
+ * filter: range classes by (n_range, range spectrum), azimuth classes by (L,
+ * azimuth spectrum)), build each class's filter and twiddle tables, and
+ * capture the whole batch into one CUDA graph.
+ * flags 0: the graph is one memset and ONE persistent kernel.  Each resident
+ * block (one per SM) takes work items from one list: range items (k azimuth
+ * rows of a strip, k = 16384 / n_range, compressed along range and written
+ * straight into the corner-turned image, Sec. IV-A steps 1-2) and azimuth
+ * items (k range bins, compressed along azimuth in place, Sec. IV-A step 4).
+ * A strip's azimuth items wait on a device counter of its finished range
+ * lines; that wait is bounded (about a second of SM clock, SAR_WAIT_CYCLES),
+ * and a run whose wait ran out is reported by sar_batch_status.  No work
+ * buffer.
+ * flags SAR_BATCH_MULTI_KERNEL or SAR_BATCH_EXACT_AZIMUTH: see below (one
+ * launch per class, a batched corner turn, a work buffer of 8 bytes per raw
+ * sample).
  * The strip buffers stay owned by the caller and must outlive the batch; the
- * spectra are copied.  flags: 0 or SAR_BATCH_EXACT_AZIMUTH.  Synchronises the
- * device. */
+ * spectra are copied.  Synchronises the device. */
 /* Azimuth lines compressed at exactly their n_az samples (the circular
  * correlation at n_az, as a plan of that length computes it) instead of
  * zero-padded to L: az_spectrum holds n_az values, classes are (n_az, azimuth
@@ -353,11 +364,27 @@ typedef struct {
  * zero-padded linear convolution of sar_plan_create, one launch per strip in
  * the graph. */
 #define SAR_BATCH_EXACT_AZIMUTH 1u
+/* The multi-kernel graph instead of the one persistent kernel, with the same
+ * (zero-padded) semantics: one fused launch per class walking a segment
+ * table, one batched corner turn, a work buffer of 8 bytes per raw sample.
+ * On GB300 it runs the config-4 batch faster than the one-launch kernel,
+ * whose blocks are sized for 16384-sample lines (one per SM, the lines of an
+ * item advancing together), while the per-class kernels run four or five
+ * blocks per SM. */
+#define SAR_BATCH_MULTI_KERNEL 2u
 SAR_API sar_status sar_batch_create(const sar_strip *strips, int32_t count, uint32_t flags, sar_batch *out);
 
-/* Compress every strip of the batch: one graph launch on `stream` (range
- * passes, one corner turn over all strips, azimuth passes); asynchronous. */
+/* Compress every strip of the batch: one graph launch on `stream`;
+ * asynchronous. */
 SAR_API sar_status sar_batch_run(sar_batch batch, sar_stream stream);
+
+/* Synchronise `stream` and report whether a bounded device wait of the
+ * one-launch batch kernel ran out in a run since the last call:
+ * SAR_ERR_TIMEOUT (the record is then cleared; the images of that run are
+ * incomplete, the context stays usable), else SAR_OK.  Every block stops
+ * taking work items once a wait has run out, so such a run ends within about
+ * one wait bound. */
+SAR_API sar_status sar_batch_status(sar_batch batch, sar_stream stream);
 
 /* Sizes of a batch. */
 SAR_API sar_status sar_batch_info(sar_batch batch, sar_batch_info_t *info);

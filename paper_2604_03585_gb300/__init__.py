@@ -29,6 +29,7 @@ SAR_PREC_FP32, SAR_PREC_FP16X2, SAR_PREC_BF16X2, SAR_PREC_BF16X3 = 0, 1, 2, 3
 SAR_PLAN_UNFOLDED_CORNER_TURN = 1
 SAR_PLAN_OUT_AZ_MAJOR = 2
 SAR_BATCH_EXACT_AZIMUTH = 1
+SAR_BATCH_MULTI_KERNEL = 2
 SAR_TUNE_FUSED, SAR_TUNE_RANGE_CT = 0, 1
 SAR_SERVE_OPEN_LOOP, SAR_SERVE_CLOSED_LOOP = 0, 1
 
@@ -43,7 +44,7 @@ EXPORTS = ("sar_plan_create", "sar_plan_destroy", "sar_range_compress", "sar_cor
            "sar_rda_process_host", "sar_rda_process_host_n", "sar_make_lfm_spectrum", "sar_simulate_echo",
            "sar_fft_lines", "sar_fft_lines_static", "sar_transpose", "sar_schedule_count", "sar_schedule_get",
            "sar_set_preferred_schedule", "sar_set_corner_turn_variant", "sar_plan_create_ex", "sar_plan_get_schedules", "sar_plan_folds_corner_turn", "sar_autotune",
-           "sar_plan_status", "sar_batch_create", "sar_batch_run", "sar_batch_info",
+           "sar_plan_status", "sar_batch_create", "sar_batch_run", "sar_batch_info", "sar_batch_status",
            "sar_batch_destroy", "sar_server_create", "sar_server_run", "sar_server_destroy",
            "sar_sync", "sar_last_error", "sar_version")
 
@@ -120,6 +121,7 @@ _SIGS = {
     "sar_plan_status": [_vp, _vp],
     "sar_batch_create": [ctypes.POINTER(sar_strip), ctypes.c_int32, ctypes.c_uint32, ctypes.POINTER(_vp)],
     "sar_batch_run": [_vp, _vp],
+    "sar_batch_status": [_vp, _vp],
     "sar_batch_info": [_vp, ctypes.POINTER(sar_batch_info_t)],
     "sar_batch_destroy": [_vp],
     "sar_server_create": [ctypes.POINTER(sar_server_config), ctypes.POINTER(_vp)],
@@ -418,6 +420,12 @@ def sar_batch_create(strips, flags: int = 0) -> Batch:
 
 def sar_batch_run(batch, stream=None) -> None:
     _check(_lib.sar_batch_run(_h(batch), _stream(stream)))
+
+
+def sar_batch_status(batch, stream=None) -> None:
+    """Raises SarError(SAR_ERR_TIMEOUT) if a bounded wait of the batch kernel
+    ran out since the last call (the record is cleared)."""
+    _check(_lib.sar_batch_status(_h(batch), _stream(stream)))
 
 
 def sar_batch_info(batch) -> dict:

@@ -3,24 +3,35 @@
 //
 // A strip is an n_az x n_range raw echo (n_range a power of two, n_az any
 // count); its azimuth lines are transformed at L = max(256, next power of
-// two >= n_az), zero-padded, and the image keeps its n_az columns.  Strips
-// are grouped into classes that share a kernel and a filter: range classes by
-// (n_range, range spectrum), azimuth classes by (L, azimuth spectrum).  One
-// fused launch per class walks a segment table (one segment per strip, the
-// strip's lines concatenated); one batched transpose walks a tile table over
-// all strips.  The whole sequence is captured once into a CUDA graph and
-// replayed by sar_batch_run as a single launch.
+// two >= n_az), zero-padded, and the image keeps its n_az columns.
 //
-// Data path per strip: range compression raw -> work (batch-owned scratch),
+// Default: one persistent kernel (batch_persistent.cu) walks a list of work
+// items -- range items (k azimuth rows of a strip, compressed along range and
+// written corner-turned into the image) and azimuth items (k range bins,
+// compressed in place) -- with per-strip completion counters between a
+// strip's range and azimuth items.  The graph is one memset of the counters
+// and that one kernel.  Filters and twiddles are built per class: range
+// classes by (n_range, range spectrum), azimuth classes by (L, azimuth
+// spectrum), on the kernel's engine geometry of each length.
+//
+// SAR_BATCH_MULTI_KERNEL, and SAR_BATCH_EXACT_AZIMUTH (azimuth lines at
+// exactly n_az, which needs the zero-padded linear convolution of lengths
+// that are not powers of two): one fused launch per class walking a segment
+// table (one segment per strip,
+// the strip's lines concatenated), one batched transpose over all strips, and
+// for such lengths one launch per strip, all captured into one graph.  Data
+// path per strip there: range compression raw -> work (batch-owned scratch),
 // corner turn work -> image, azimuth compression in place on image.  The raw
-// echo is only read.
+// echo is only read on both paths.
 #include <algorithm>
+#include <stdlib.h>
 #include <new>
 #include <stdio.h>
 #include <string.h>
 #include <vector>
 
 #include "../../include/sar.h"
+#include "batch_persistent.h"
 #include "registry.h"
 #include "streamed.cuh"
 #include "tables.h"
@@ -114,6 +125,10 @@ struct sar_batch_s {
     int64_t samples = 0;       // sum of n_az * n_range
     int32_t launches = 0;      // kernels in the graph
     int64_t strips = 0;
+    // one-launch path
+    bool persistent = false;
+    int32_t n_range_classes = 0, n_az_classes = 0;
+    int *status_dev = nullptr;  // 5 after a timed-out wait (sticky until sar_batch_status)
 };
 
 static void batch_free(sar_batch b) {
@@ -125,14 +140,179 @@ static void batch_free(sar_batch b) {
     delete b;
 }
 
+// Bound of the batch kernel's waits: about one second at the GB300's maximum
+// SM clock, or SAR_WAIT_CYCLES.
+static long long batch_wait_cycles() {
+    const char *v = getenv("SAR_WAIT_CYCLES");
+    const long long c = v ? atoll(v) : 0;
+    return c > 0 ? c : 2000000000LL;
+}
+
+// Test hook (host-side fault injection): SAR_FAULT_INJECT_BATCH_WAIT=<i> makes
+// batches created while it is set expect one range line more of strip i than
+// it has, so that strip's completion counter never reaches its target and the
+// kernel's bounded wait runs out.
+static int64_t batch_inject_strip() {
+    const char *v = getenv("SAR_FAULT_INJECT_BATCH_WAIT");
+    return v ? atoll(v) : -1;
+}
+
+// The one-launch batch: classes and their tables, the strip and item tables,
+// and a graph of one memset (the counters) and one kernel.
+static sar_status create_persistent(const sar_strip *strips, int32_t count, sar_batch b) {
+    struct TClass {
+        const SchedDesc *d;
+        const void *spectrum;
+        int64_t n;
+        bool range;
+        float2 *filt = nullptr, *tw = nullptr;
+    };
+    std::vector<TClass> cls;
+    auto class_of = [&](int64_t n, const void *spec, bool range) -> int {
+        for (size_t i = 0; i < cls.size(); ++i)
+            if (cls[i].n == n && cls[i].spectrum == spec && cls[i].range == range) return (int)i;
+        const char *name = sar::batch_schedule_name((int)n);
+        const SchedDesc *d = name ? sar::find_schedule(name) : nullptr;
+        if (!d) return -1;
+        cls.push_back(TClass{d, spec, n, range});
+        if (range)
+            ++b->n_range_classes;
+        else
+            ++b->n_az_classes;
+        return (int)cls.size() - 1;
+    };
+    std::vector<int> rc(count), ac(count);
+    std::vector<int64_t> L(count);
+    for (int32_t i = 0; i < count; ++i) {
+        L[i] = std::max<int64_t>(256, next_pow2(strips[i].n_az));
+        if (L[i] > 16384) return sar::report_error(SAR_ERR_UNSUPPORTED, "azimuth transform length above 16384");
+        rc[i] = class_of(strips[i].n_range, strips[i].range_spectrum, true);
+        ac[i] = class_of(L[i], strips[i].az_spectrum, false);
+        if (rc[i] < 0 || ac[i] < 0) return sar::report_error(SAR_ERR_UNSUPPORTED, "no batch engine for a strip length");
+    }
+    // item list: strips largest first; range items of strip j + 1 before the
+    // azimuth items of strip j, so that an azimuth item's strip is finished
+    // (or being finished by blocks that took its items earlier) when a block
+    // takes it
+    std::vector<int32_t> order(count);
+    for (int32_t i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+        return strips[x].n_az * strips[x].n_range > strips[y].n_az * strips[y].n_range;
+    });
+    std::vector<sar::BItem> items;
+    auto add_range = [&](int32_t i) {
+        const int k = sar::batch_lines_per_item((int)strips[i].n_range);
+        for (int64_t a = 0; a < strips[i].n_az; a += k)
+            items.push_back(sar::BItem{0, i, (int32_t)a, (int32_t)std::min<int64_t>(k, strips[i].n_az - a)});
+    };
+    auto add_az = [&](int32_t i) {
+        const int k = sar::batch_lines_per_item((int)L[i]);
+        for (int64_t r = 0; r < strips[i].n_range; r += k)
+            items.push_back(sar::BItem{1, i, (int32_t)r, (int32_t)std::min<int64_t>(k, strips[i].n_range - r)});
+    };
+    for (int32_t j = 0; j < count; ++j) {
+        add_range(order[j]);
+        if (j > 0) add_az(order[j - 1]);
+    }
+    add_az(order[count - 1]);
+    if (items.size() > (size_t)0x7fffffff) return sar::report_error(SAR_ERR_UNSUPPORTED, "too many work items");
+
+    // ---- device memory: tables, strips, items, counters, status
+    size_t tab = 0;
+    auto reserve = [&](size_t bytes) {
+        const size_t o = tab;
+        tab += align_up(bytes);
+        return o;
+    };
+    std::vector<size_t> off_f, off_t;
+    int64_t max_n = 0;
+    for (auto &c : cls) {
+        off_f.push_back(reserve(sizeof(float2) * c.d->n));
+        off_t.push_back(reserve(sizeof(float2) * c.d->tw_elems));
+        max_n = std::max<int64_t>(max_n, c.d->n);
+    }
+    const size_t off_st = reserve(sizeof(sar::BStrip) * count);
+    const size_t off_it = reserve(sizeof(sar::BItem) * items.size());
+    const size_t off_ctr = reserve(sizeof(int) * ((size_t)count + 1));
+    const size_t off_status = reserve(sizeof(int));
+    const size_t off_ix = reserve(sizeof(int32_t) * max_n);
+    if (cudaMalloc(&b->tables, tab) != cudaSuccess) {
+        cudaGetLastError();
+        return sar::report_error(SAR_ERR_OUT_OF_MEMORY, "batch tables");
+    }
+    char *base = (char *)b->tables;
+    sar::BStrip *strips_dev = (sar::BStrip *)(base + off_st);
+    sar::BItem *items_dev = (sar::BItem *)(base + off_it);
+    int *counters = (int *)(base + off_ctr);
+    b->status_dev = (int *)(base + off_status);
+    int32_t *idx_dev = (int32_t *)(base + off_ix);
+
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();   // the caller's spectra are ready
+    if (e == cudaSuccess) e = sar::prepare_batch_persistent();
+    std::vector<int32_t> idx;
+    for (size_t ci = 0; ci < cls.size() && e == cudaSuccess; ++ci) {
+        TClass &c = cls[ci];
+        c.filt = (float2 *)(base + off_f[ci]);
+        c.tw = (float2 *)(base + off_t[ci]);
+        if ((e = c.d->prepare()) != cudaSuccess) break;
+        if ((e = sar::build_twiddles(*c.d, c.tw, s)) != cudaSuccess) break;
+        idx.assign(c.d->n, 0);
+        sar::filter_slot_to_k(*c.d, idx.data());
+        if ((e = cudaMemcpyAsync(idx_dev, idx.data(), sizeof(int32_t) * c.d->n, cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess)
+            break;
+        if ((e = sar::build_filter(*c.d, (const float2 *)c.spectrum, c.filt, idx_dev, s)) != cudaSuccess) break;
+        e = cudaStreamSynchronize(s);   // idx is reused by the next class
+    }
+    const int64_t inject = batch_inject_strip();
+    std::vector<sar::BStrip> bs(count);
+    for (int32_t i = 0; i < count; ++i) {
+        const sar_strip &st = strips[i];
+        bs[i] = sar::BStrip{(const float2 *)st.raw, (float2 *)st.image, cls[rc[i]].filt, cls[rc[i]].tw,
+                            cls[ac[i]].filt, cls[ac[i]].tw, (int32_t)st.n_range, (int32_t)st.n_az, (int32_t)L[i],
+                            (int32_t)st.n_az + (i == inject ? 1 : 0)};
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(strips_dev, bs.data(), sizeof(sar::BStrip) * count, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(items_dev, items.data(), sizeof(sar::BItem) * items.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->status_dev, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    // ---- the graph: clear the counters, one kernel
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t le = cudaMemsetAsync(counters, 0, sizeof(int) * ((size_t)count + 1), s);
+        if (le == cudaSuccess)
+            le = sar::launch_batch_persistent(items_dev, (int)items.size(), strips_dev, counters, counters + count,
+                                              b->status_dev, batch_wait_cycles(), s);
+        b->launches = 1;
+        e = cudaStreamEndCapture(s, &b->graph);
+        if (e == cudaSuccess && le != cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (s) cudaStreamDestroy(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        char msg[256];
+        snprintf(msg, sizeof(msg), "batch set-up failed: %s", cudaGetErrorString(e));
+        return sar::report_error(SAR_ERR_CUDA, msg);
+    }
+    b->persistent = true;
+    return SAR_OK;
+}
+
 extern "C" {
 
 sar_status sar_batch_create(const sar_strip *strips, int32_t count, uint32_t flags, sar_batch *out) {
     if (!out) return sar::report_error(SAR_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!strips || count < 1) return sar::report_error(SAR_ERR_INVALID_ARG, "need at least one strip");
-    if (flags & ~SAR_BATCH_EXACT_AZIMUTH) return sar::report_error(SAR_ERR_INVALID_ARG, "unknown flags");
+    if (flags & ~(SAR_BATCH_EXACT_AZIMUTH | SAR_BATCH_MULTI_KERNEL))
+        return sar::report_error(SAR_ERR_INVALID_ARG, "unknown flags");
     const bool exact = (flags & SAR_BATCH_EXACT_AZIMUTH) != 0;
+    const bool multi = exact || (flags & SAR_BATCH_MULTI_KERNEL) != 0;
     sar_status st;
     for (int32_t i = 0; i < count; ++i) {
         const sar_strip &s = strips[i];
@@ -154,6 +334,16 @@ sar_status sar_batch_create(const sar_strip *strips, int32_t count, uint32_t fla
     if (!b) return sar::report_error(SAR_ERR_OUT_OF_MEMORY, "host allocation failed");
     cudaGetDevice(&b->device);
     b->strips = count;
+    if (!multi) {
+        for (int32_t i = 0; i < count; ++i) b->samples += strips[i].n_az * strips[i].n_range;
+        const sar_status pst = create_persistent(strips, count, b);
+        if (pst != SAR_OK) {
+            batch_free(b);
+            return pst;
+        }
+        *out = b;
+        return SAR_OK;
+    }
 
     // ---- classes and segment tables (host side)
     size_t work_elems = 0;
@@ -371,10 +561,26 @@ sar_status sar_batch_info(sar_batch b, sar_batch_info_t *info) {
     info->strips = b->strips;
     info->samples = b->samples;
     info->kernels_per_run = b->launches;
-    info->range_classes = (int32_t)b->range.size();
-    info->azimuth_classes = (int32_t)b->az.size();
-    info->work_bytes = b->samples * 8;
+    info->range_classes = b->persistent ? b->n_range_classes : (int32_t)b->range.size();
+    info->azimuth_classes = b->persistent ? b->n_az_classes : (int32_t)b->az.size();
+    info->work_bytes = b->persistent ? 0 : b->samples * 8;
     return SAR_OK;
+}
+
+sar_status sar_batch_status(sar_batch b, sar_stream stream) {
+    if (!b) return sar::report_error(SAR_ERR_INVALID_ARG, "batch is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return sar::report_error(SAR_ERR_CUDA, cudaGetErrorString(e));
+    if (!b->status_dev) return SAR_OK;
+    int v = 0;
+    if ((e = cudaMemcpy(&v, b->status_dev, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return sar::report_error(SAR_ERR_CUDA, cudaGetErrorString(e));
+    if (v == 0) return SAR_OK;
+    if ((e = cudaMemset(b->status_dev, 0, sizeof(int))) != cudaSuccess)
+        return sar::report_error(SAR_ERR_CUDA, cudaGetErrorString(e));
+    return sar::report_error(SAR_ERR_TIMEOUT, "a bounded wait of the batch kernel ran out (a strip's range lines "
+                                              "never all completed); the images of that run are incomplete");
 }
 
 sar_status sar_batch_destroy(sar_batch b) {

@@ -66,16 +66,21 @@ __device__ __forceinline__ void streamed_mid_pass(float2* sm, const float2* tw, 
 // Element i of a line that holds `valid` stored samples (zero beyond them:
 // a zero-padded transform of a ragged line).
 // Line samples are read once: streaming loads (evict-first), so that they
-// do not push the twiddle and filter tables out of L1.
-template <bool RAGGED>
+// do not push the twiddle and filter tables out of L1.  With L2ONLY the loads
+// bypass L1 (ld.global.cg): for data that other SMs wrote earlier in the same
+// launch, where an L1 line cached before the write could be stale.
+template <bool RAGGED, bool L2ONLY = false>
 __device__ __forceinline__ float2 line_at(const float2* src, int i, int valid) {
-    if constexpr (RAGGED)
-        return i < valid ? __ldcs(src + i) : make_float2(0.f, 0.f);
+    if constexpr (RAGGED) {
+        if (i >= valid) return make_float2(0.f, 0.f);
+    }
+    if constexpr (L2ONLY)
+        return __ldcg(src + i);
     else
         return __ldcs(src + i);
 }
 
-template <class SC, int LPB, bool ROLL, bool RAGGED = false>
+template <class SC, int LPB, bool ROLL, bool RAGGED = false, bool L2ONLY = false>
 __device__ __forceinline__ void streamed_until_last(const float2* src, float2* sm, const float2* filt,
                                                     const float2* tw, int t, int lib, int valid = SC::N) {
     constexpr int R1 = SC::R1, S1 = SC::S1, G1 = SC::E / R1;
@@ -85,14 +90,14 @@ __device__ __forceinline__ void streamed_until_last(const float2* src, float2* s
     //      next group's loads in flight during the current group's arithmetic
     float2 cur[R1];
 #pragma unroll
-    for (int r = 0; r < R1; ++r) cur[r] = line_at<RAGGED>(src, t + r * S1, valid);
+    for (int r = 0; r < R1; ++r) cur[r] = line_at<RAGGED, L2ONLY>(src, t + r * S1, valid);
 #pragma unroll(ROLL ? 1 : G1)
     for (int s = 0; s < G1; ++s) {
         const int lo = t + SC::T * s;
         float2 nxt[R1];
         if (s + 1 < G1) {
 #pragma unroll
-            for (int r = 0; r < R1; ++r) nxt[r] = line_at<RAGGED>(src, lo + SC::T + r * S1, valid);
+            for (int r = 0; r < R1; ++r) nxt[r] = line_at<RAGGED, L2ONLY>(src, lo + SC::T + r * S1, valid);
         }
         dft_reg<R1, false>(cur);
         grp_twiddle<R1, S1, false>(tw, lo, cur);

@@ -71,8 +71,10 @@ def test_ragged_batch_vs_oracle(sar):
     assert info["strips"] == len(shapes)
     assert info["samples"] == sum(a * b for a, b in shapes)
     assert info["range_classes"] == 5 and info["azimuth_classes"] == 4
+    assert info["kernels_per_run"] == 1          # one persistent launch
     sar.sar_batch_run(batch)
     sar.sar_sync()
+    sar.sar_batch_status(batch)
     for (raw, raw_d, img_d), spec, st in zip(keep, specs, strips):
         img = img_d.cpu().numpy()
         assert np.array_equal(raw_d.cpu().numpy(), raw)            # raw is read only
@@ -90,6 +92,87 @@ def test_ragged_batch_vs_oracle(sar):
     for a, k in zip(first, keep):
         assert torch.equal(a, k[2])
     batch.destroy()
+
+
+def test_ragged_batch_long_range_lines_vs_oracle(sar):
+    """Strips with range lines of 8192 and 16384 samples (one and two lines
+    per work item, the engines with the most registers per thread) beside
+    short ones, ragged azimuth counts, against the oracle."""
+    orc = oracle.default()
+    shapes = [(16384, 300), (8192, 517), (1024, 64), (16384, 129), (4096, 256), (8192, 40)]
+    strips, keep, specs, hr, ha = make_strips(sar, orc, shapes, seed=7)
+    batch = sar.sar_batch_create(strips)
+    assert sar.sar_batch_info(batch)["kernels_per_run"] == 1
+    sar.sar_batch_run(batch)
+    sar.sar_batch_status(batch)
+    for (raw, raw_d, img_d), spec in zip(keep, specs):
+        img = img_d.cpu().numpy()
+        Hr = hr[spec.n_range].cpu().numpy().astype(np.complex128)
+        Ha = ha[spec.l_az].cpu().numpy().astype(np.complex128)
+        ref = orc.rda(raw, Hr, Ha, l_az=spec.l_az, nthreads=NTHREADS)
+        assert M.rel_l2(img, ref) < 2e-5, (spec.n_range, spec.n_az)
+        for (a0, r0) in spec.targets:
+            if spec.n_az >= 64:
+                assert M.peak(img, (r0, a0)) == M.peak(ref, (r0, a0))
+    batch.destroy()
+
+
+def test_one_launch_equals_multi_kernel_graph(sar):
+    """The one persistent kernel and the multi-kernel graph run the same line
+    engines (same geometry, twiddles and filter order per length) and the
+    corner turn is a copy either way: the images are bit-identical."""
+    orc = oracle.default()
+    shapes = [(1024, 300), (256, 256), (4096, 777), (2048, 129), (512, 4096), (8192, 100), (16384, 33)]
+    strips, keep, specs, hr, ha = make_strips(sar, orc, shapes, seed=8)
+    one = sar.sar_batch_create(strips)
+    multi = sar.sar_batch_create(strips, flags=sar.SAR_BATCH_MULTI_KERNEL)
+    assert sar.sar_batch_info(one)["kernels_per_run"] == 1
+    assert sar.sar_batch_info(multi)["kernels_per_run"] > 1
+    sar.sar_batch_run(one)
+    sar.sar_batch_status(one)
+    first = [k[2].clone() for k in keep]
+    sar.sar_batch_run(multi)
+    sar.sar_sync()
+    for a, k, spec in zip(first, keep, specs):
+        assert torch.equal(a, k[2]), (spec.n_range, spec.n_az)
+    one.destroy()
+    multi.destroy()
+
+
+def test_ragged_batch_wait_timeout_is_reported(sar):
+    """A strip whose completion counter can never reach its target
+    (host-side injection: one range line more expected than it has) makes the
+    azimuth items' bounded wait run out: sar_batch_status reports
+    SAR_ERR_TIMEOUT within the bound, the record is cleared, the context stays
+    usable and a batch created without the injection computes normally."""
+    orc = oracle.default()
+    shapes = [(1024, 300), (2048, 129), (4096, 64)]
+    strips, keep, specs, hr, ha = make_strips(sar, orc, shapes, seed=9)
+    os.environ["SAR_FAULT_INJECT_BATCH_WAIT"] = "1"
+    os.environ["SAR_WAIT_CYCLES"] = "20000000"          # about ten milliseconds
+    try:
+        bad = sar.sar_batch_create(strips)
+    finally:
+        del os.environ["SAR_FAULT_INJECT_BATCH_WAIT"]
+        del os.environ["SAR_WAIT_CYCLES"]
+    import time
+    t0 = time.perf_counter()
+    sar.sar_batch_run(bad)
+    with pytest.raises(sar.SarError) as e:
+        sar.sar_batch_status(bad)
+    assert e.value.status == sar.SAR_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    sar.sar_batch_status(bad)                            # the record was cleared
+    bad.destroy()
+    good = sar.sar_batch_create(strips)
+    sar.sar_batch_run(good)
+    sar.sar_batch_status(good)
+    for (raw, raw_d, img_d), spec in zip(keep, specs):
+        Hr = hr[spec.n_range].cpu().numpy().astype(np.complex128)
+        Ha = ha[spec.l_az].cpu().numpy().astype(np.complex128)
+        ref = orc.rda(raw, Hr, Ha, l_az=spec.l_az, nthreads=NTHREADS)
+        assert M.rel_l2(img_d.cpu().numpy(), ref) < 2e-5
+    good.destroy()
 
 
 def test_batch_refuses_bad_strips(sar):
