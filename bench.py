@@ -450,17 +450,18 @@ def unfused_bench(sar, plan, raw, work, image, stream, fused_ms: float, reps: in
 
 def precision_bench(sar, Hr, Ha, raw, work, image, stream, reps: int = 50) -> dict:
     """Time the 4096^2 scene with each split-precision plan (three kernels:
-    range pass, corner turn, azimuth pass) and the FP32 plan through the same
-    unfolded path; the images are compared with the FP32 image here and with
-    the FP64 oracle in tests/test_gpu_parity.py."""
+    range pass, corner turn, azimuth pass) on both tensor-core engines
+    (tcgen05.mma with TMEM accumulators, the default; warp-level mma.sync),
+    and the FP32 plan through the same unfolded path; the images are compared
+    with the FP32 image here and with the FP64 oracle in
+    tests/test_gpu_parity.py."""
     import torch
     out = {}
     ref = None
-    for name in ("FP32", "FP16X2", "BF16X2", "BF16X3"):
-        code = getattr(sar, "SAR_PREC_" + name)
-        plan = sar.sar_plan_create(N_RANGE, N_AZ, Hr, Ha, precision=code, flags=sar.SAR_PLAN_UNFOLDED_CORNER_TURN)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(plan):
         times = []
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         for i in range(reps + 3):
             e0.record(stream)
             sar.sar_rda_process_oop(plan, raw, work, image, stream)
@@ -469,11 +470,26 @@ def precision_bench(sar, Hr, Ha, raw, work, image, stream, reps: int = 50) -> di
             if i >= 3:
                 times.append(e0.elapsed_time(e1))
         times.sort()
-        img = image.clone()
-        if ref is None:
-            ref = img
-        diff = float(torch.linalg.vector_norm(img - ref) / torch.linalg.vector_norm(ref))
-        out[name] = {"ms_per_scene": times[len(times) // 2], "rel_l2_vs_fp32_path": diff}
+        return times[len(times) // 2]
+
+    for name in ("FP32", "FP16X2", "BF16X2", "BF16X3"):
+        code = getattr(sar, "SAR_PREC_" + name)
+        plan = sar.sar_plan_create(N_RANGE, N_AZ, Hr, Ha, precision=code, flags=sar.SAR_PLAN_UNFOLDED_CORNER_TURN)
+        engines = (("tcgen05", 0), ("mma_sync", 1)) if name != "FP32" else (("fp32", 0),)
+        row = {}
+        for ename, eng in engines:
+            sar.sar_set_split_engine(eng)
+            try:
+                ms = timed(plan)
+                sar.sar_plan_status(plan, stream)
+            finally:
+                sar.sar_set_split_engine(0)
+            img = image.clone()
+            if ref is None:
+                ref = img
+            diff = float(torch.linalg.vector_norm(img - ref) / torch.linalg.vector_norm(ref))
+            row[ename] = {"ms_per_scene": ms, "rel_l2_vs_fp32_path": diff}
+        out[name] = row if name != "FP32" else row["fp32"]
         plan.destroy()
     out["note"] = ("unfolded three-kernel path for every precision; the error against the FP64 oracle "
                    "is checked by the parity tests")

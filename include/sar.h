@@ -511,6 +511,14 @@ SAR_API int32_t sar_plan_folds_corner_turn(sar_plan plan);
 /* The schedules a plan runs. */
 SAR_API sar_status sar_plan_get_schedules(sar_plan plan, sar_schedule_desc *range, sar_schedule_desc *az);
 
+/* Engine of the split-precision plans (process-wide, thread-safe; takes
+ * effect at the next launch): 0 = every radix-16 DFT as tcgen05.mma on the
+ * fifth-generation tensor cores, 128 groups x 32 x 32 per instruction with
+ * FP32 accumulators in tensor memory (the default); 1 = the warp-level
+ * mma.sync.m16n8k16 form, 8 groups per instruction.  Same products, scaling
+ * and results within rounding.  SAR_ERR_INVALID_ARG for any other value. */
+SAR_API sar_status sar_set_split_engine(int32_t engine);
+
 /* Time every compiled schedule of length n (reps launches each, CUDA events
  * on `stream`, median) and make the fastest the preferred schedule of n for
  * that kind of kernel:

@@ -43,7 +43,7 @@ EXPORTS = ("sar_plan_create", "sar_plan_destroy", "sar_range_compress", "sar_cor
            "sar_plan_set_geometry", "sar_rcmc", "sar_rda_full",
            "sar_rda_process_host", "sar_rda_process_host_n", "sar_make_lfm_spectrum", "sar_simulate_echo",
            "sar_fft_lines", "sar_fft_lines_static", "sar_transpose", "sar_schedule_count", "sar_schedule_get",
-           "sar_set_preferred_schedule", "sar_set_corner_turn_variant", "sar_plan_create_ex", "sar_plan_get_schedules", "sar_plan_folds_corner_turn", "sar_autotune",
+           "sar_set_preferred_schedule", "sar_set_corner_turn_variant", "sar_set_split_engine", "sar_plan_create_ex", "sar_plan_get_schedules", "sar_plan_folds_corner_turn", "sar_autotune",
            "sar_plan_status", "sar_batch_create", "sar_batch_run", "sar_batch_info", "sar_batch_status",
            "sar_batch_destroy", "sar_server_create", "sar_server_run", "sar_server_destroy",
            "sar_sync", "sar_last_error", "sar_version")
@@ -131,6 +131,7 @@ _SIGS = {
     "sar_schedule_get": [ctypes.c_int32, ctypes.POINTER(sar_schedule_desc)],
     "sar_set_preferred_schedule": [ctypes.c_char_p],
     "sar_set_corner_turn_variant": [ctypes.c_int32],
+    "sar_set_split_engine": [ctypes.c_int32],
     "sar_plan_create_ex": [_i64, _i64, ctypes.POINTER(sar_filters), ctypes.c_char_p, ctypes.c_char_p,
                            ctypes.POINTER(_vp)],
     "sar_plan_get_schedules": [_vp, ctypes.POINTER(sar_schedule_desc), ctypes.POINTER(sar_schedule_desc)],
@@ -264,6 +265,11 @@ def sar_set_preferred_schedule(name: str) -> None:
 
 def sar_set_corner_turn_variant(variant: int) -> None:
     _check(_lib.sar_set_corner_turn_variant(variant))
+
+
+def sar_set_split_engine(engine: int) -> None:
+    """Engine of split-precision plans: 0 tcgen05.mma (TMEM accumulators), 1 mma.sync."""
+    _check(_lib.sar_set_split_engine(engine))
 
 
 def sar_autotune(n: int, n_lines: int, reps: int = 20, stream=None, kind: int = SAR_TUNE_FUSED) -> tuple:

@@ -2,6 +2,7 @@
 // declared in include/sar.h.  All compute runs in this library's kernels;
 // there is no host or library fallback.
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <stdarg.h>
@@ -260,6 +261,10 @@ struct sar_plan_s {
     int rcmc_rows = 0;   // input rows one RCMC tile stages in shared memory
 };
 
+// Engine of the split-precision plans (process-wide): 0 = tcgen05.mma with
+// TMEM accumulators, 1 = warp-level mma.sync.
+static std::atomic<int> g_split_engine{0};
+
 extern "C" {
 
 const char *sar_last_error(void) { return g_last_error.c_str(); }
@@ -464,6 +469,12 @@ sar_status sar_set_corner_turn_variant(int32_t v) {
 
 int32_t sar_plan_folds_corner_turn(sar_plan p) { return p && p->fold ? 1 : 0; }
 
+sar_status sar_set_split_engine(int32_t engine) {
+    if (engine != 0 && engine != 1) return fail(SAR_ERR_INVALID_ARG, "split engine must be 0 or 1, not %d", engine);
+    g_split_engine.store(engine);
+    return SAR_OK;
+}
+
 sar_status sar_plan_get_schedules(sar_plan p, sar_schedule_desc *range, sar_schedule_desc *az) {
     if (!p) return fail(SAR_ERR_INVALID_ARG, "plan is NULL");
     if (range) describe(*p->range.sched, range);
@@ -584,8 +595,12 @@ static sar_status run_fused(const sar_plan_s *p, const LinePlan &lp, int64_t n_l
                             cudaStream_t s, const char *what) {
     const SchedDesc &d = *lp.sched;
     if (p->prec != SAR_PREC_FP32) {
-        cudaError_t e = sar::launch_mma_compress(d.n, p->prec, (const float2 *)in, (float2 *)out, n_lines, d.n,
-                                                 lp.filt, lp.tw, s);
+        cudaError_t e =
+            g_split_engine.load() == 1
+                ? sar::launch_mma_compress(d.n, p->prec, (const float2 *)in, (float2 *)out, n_lines, d.n, lp.filt,
+                                           lp.tw, s)
+                : sar::launch_mma_tc_compress(d.n, p->prec, (const float2 *)in, (float2 *)out, n_lines, d.n, lp.filt,
+                                              lp.tw, p->ctl.status, p->ctl.wait_cycles, s);
         if (e != cudaSuccess) return cuda_fail(e, what);
         return SAR_OK;
     }

@@ -577,13 +577,15 @@ def test_empty_inputs(sar):
 PREC_GATES = {"FP16X2": 2e-5, "BF16X3": 2e-5, "BF16X2": 2e-4}
 
 
+@pytest.mark.parametrize("engine", [0, 1], ids=["tcgen05", "mma_sync"])
 @pytest.mark.parametrize("prec", ["FP16X2", "BF16X2", "BF16X3"])
 @pytest.mark.parametrize("make", [sarsim.scene_256, sarsim.scene_4096], ids=["256", "4096"])
-def test_split_precision_vs_oracle(sar, orc, prec, make):
+def test_split_precision_vs_oracle(sar, orc, prec, make, engine):
     """Error of each split-precision variant against the FP64 oracle, stated
     for the record (rel-L2, peaks, PSLR/ISLR/SNR deltas); FP16 hi/lo and
     BF16 hi/mid/lo meet the image gate, BF16 hi/lo is reported with its own
-    (looser) bound."""
+    (looser) bound.  Both engines: tcgen05.mma with TMEM accumulators (the
+    default) and the warp-level mma.sync form."""
     spec = make()
     Hr, Ha = gpu_filters(sar, spec)
     raw = sarsim.echo(spec)
@@ -592,7 +594,12 @@ def test_split_precision_vs_oracle(sar, orc, prec, make):
     assert not sar.sar_plan_folds_corner_turn(plan)
     raw_d = dev(raw)
     img_d = empty_c64(spec.n_range, spec.n_az)
-    sar.sar_rda_process(plan, raw_d, img_d)
+    sar.sar_set_split_engine(engine)
+    try:
+        sar.sar_rda_process(plan, raw_d, img_d)
+        sar.sar_plan_status(plan)
+    finally:
+        sar.sar_set_split_engine(0)
     img = host(img_d)
     plan.destroy()
     ref = orc.rda(raw, *oracle_filters(orc, spec), nthreads=NTHREADS)
@@ -601,7 +608,7 @@ def test_split_precision_vs_oracle(sar, orc, prec, make):
     qg, qr = M.quality(img, tg), M.quality(ref, tg)
     worst = {k: max(abs(a[k] - b[k]) for a, b in zip(qg["targets"], qr["targets"]))
              for k in ("pslr_axis0", "pslr_axis1", "islr_axis0", "islr_axis1", "snr")}
-    print(f"\nPRECISION {prec} {spec.n_az}x{spec.n_range}: rel_l2={err:.3e} max_abs={M.max_abs(img, ref):.3e} "
+    print(f"\nPRECISION {prec} engine {engine} {spec.n_az}x{spec.n_range}: rel_l2={err:.3e} max_abs={M.max_abs(img, ref):.3e} "
           + " ".join(f"d_{k}={v:.4f}dB" for k, v in worst.items()))
     assert err <= PREC_GATES[prec], err
     for a, b in zip(qg["targets"], qr["targets"]):
@@ -617,6 +624,9 @@ def test_split_precision_refusals(sar):
     assert e.value.status == sar.SAR_ERR_UNSUPPORTED
     with pytest.raises(sar.SarError) as e:
         sar.sar_plan_create(1024, 1024, x, x, precision=9)
+    assert e.value.status == sar.SAR_ERR_INVALID_ARG
+    with pytest.raises(sar.SarError) as e:
+        sar.sar_set_split_engine(2)
     assert e.value.status == sar.SAR_ERR_INVALID_ARG
 
 
