@@ -475,7 +475,7 @@ def precision_bench(sar, Hr, Ha, raw, work, image, stream, reps: int = 50) -> di
     for name in ("FP32", "FP16X2", "BF16X2", "BF16X3"):
         code = getattr(sar, "SAR_PREC_" + name)
         plan = sar.sar_plan_create(N_RANGE, N_AZ, Hr, Ha, precision=code, flags=sar.SAR_PLAN_UNFOLDED_CORNER_TURN)
-        engines = (("tcgen05", 0), ("mma_sync", 1)) if name != "FP32" else (("fp32", 0),)
+        engines = (("tcgen05_tmem_a", 0), ("tcgen05_smem_a", 2), ("mma_sync", 1)) if name != "FP32" else (("fp32", 0),)
         row = {}
         for ename, eng in engines:
             sar.sar_set_split_engine(eng)

@@ -513,8 +513,10 @@ SAR_API sar_status sar_plan_get_schedules(sar_plan plan, sar_schedule_desc *rang
 
 /* Engine of the split-precision plans (process-wide, thread-safe; takes
  * effect at the next launch): 0 = every radix-16 DFT as tcgen05.mma on the
- * fifth-generation tensor cores, 128 groups x 32 x 32 per instruction with
- * FP32 accumulators in tensor memory (the default); 1 = the warp-level
+ * fifth-generation tensor cores, 128 groups x 32 x 32 per instruction, FP32
+ * accumulators in tensor memory and the split data written by each thread
+ * into its own tensor-memory lane as the A operand (the default); 2 = the
+ * same with the A operand in shared-memory tiles; 1 = the warp-level
  * mma.sync.m16n8k16 form, 8 groups per instruction.  Same products, scaling
  * and results within rounding.  SAR_ERR_INVALID_ARG for any other value. */
 SAR_API sar_status sar_set_split_engine(int32_t engine);

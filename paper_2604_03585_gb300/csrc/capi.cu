@@ -262,7 +262,8 @@ struct sar_plan_s {
 };
 
 // Engine of the split-precision plans (process-wide): 0 = tcgen05.mma with
-// TMEM accumulators, 1 = warp-level mma.sync.
+// TMEM accumulators and the A operand in TMEM, 1 = warp-level mma.sync,
+// 2 = tcgen05.mma with the A operand in shared memory.
 static std::atomic<int> g_split_engine{0};
 
 extern "C" {
@@ -470,7 +471,7 @@ sar_status sar_set_corner_turn_variant(int32_t v) {
 int32_t sar_plan_folds_corner_turn(sar_plan p) { return p && p->fold ? 1 : 0; }
 
 sar_status sar_set_split_engine(int32_t engine) {
-    if (engine != 0 && engine != 1) return fail(SAR_ERR_INVALID_ARG, "split engine must be 0 or 1, not %d", engine);
+    if (engine < 0 || engine > 2) return fail(SAR_ERR_INVALID_ARG, "split engine must be 0, 1 or 2, not %d", engine);
     g_split_engine.store(engine);
     return SAR_OK;
 }
@@ -599,8 +600,9 @@ static sar_status run_fused(const sar_plan_s *p, const LinePlan &lp, int64_t n_l
             g_split_engine.load() == 1
                 ? sar::launch_mma_compress(d.n, p->prec, (const float2 *)in, (float2 *)out, n_lines, d.n, lp.filt,
                                            lp.tw, s)
-                : sar::launch_mma_tc_compress(d.n, p->prec, (const float2 *)in, (float2 *)out, n_lines, d.n, lp.filt,
-                                              lp.tw, p->ctl.status, p->ctl.wait_cycles, s);
+                : sar::launch_mma_tc_compress(d.n, p->prec, g_split_engine.load() == 0, (const float2 *)in,
+                                              (float2 *)out, n_lines, d.n, lp.filt, lp.tw, p->ctl.status,
+                                              p->ctl.wait_cycles, s);
         if (e != cudaSuccess) return cuda_fail(e, what);
         return SAR_OK;
     }

@@ -65,6 +65,27 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint3
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
         : "memory");
 }
+// the same with A read from tensor memory: K = 16 16-bit elements of row m
+// in lane m, columns a .. a + 7 (two elements per 32-bit column, the even K
+// index in the low half)
+__device__ __forceinline__ void tc_mma_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+        "r"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// 16 consecutive 32-bit columns of this thread's lane
+__device__ __forceinline__ void tc_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // the mbarrier completes one arrival once every MMA this thread issued is done
 __device__ __forceinline__ void tc_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -109,7 +130,14 @@ constexpr uint32_t kLBO = 128, kSBO = 512;
 constexpr uint32_t kATile = 128 * 64;   // 128 rows x 32 K x 2 bytes
 constexpr uint32_t kBTile = 32 * 64;    // 32 rows (N) x 32 K x 2 bytes
 
-template <int N, int PREC>
+constexpr uint32_t pow2_at_least(uint32_t v) {
+    uint32_t p = 32;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+// ATM: A operand (the split groups) in tensor memory instead of shared memory
+template <int N, int PREC, bool ATM>
 struct TcGeom {
     static constexpr int LV = SplitTraits<PREC>::LEVELS;
     static constexpr int P = (N == 4096) ? 3 : 2;
@@ -119,13 +147,14 @@ struct TcGeom {
     static constexpr int MT = GT / 128;               // M tiles
     static constexpr int LINE = N + N / 16;           // padded line (one slot per 16)
     static constexpr uint32_t OFF_A = ((LPB * LINE * 8 + 1023) / 1024) * 1024;
-    static constexpr uint32_t OFF_B = OFF_A + MT * LV * kATile;
-    // 8 KiB of slack after the last operand tile: the descriptors' extents
-    // end inside their tiles, and the slack keeps any reading of them within
-    // this block's shared memory all the same
-    static constexpr uint32_t OFF_BAR = OFF_B + 2 * LV * kBTile + 8192;
+    static constexpr uint32_t OFF_B = OFF_A + (ATM ? 0 : MT * LV * kATile);
+    static constexpr uint32_t OFF_BAR = OFF_B + 2 * LV * kBTile;
     static constexpr uint32_t SMEM = OFF_BAR + 16;
-    static constexpr uint32_t TCOLS = MT * 32;       // 32 or 64: a power of two >= 32
+    // TMEM columns: the accumulators (32 per M tile), then with ATM the A
+    // operands (16 columns per tile and split level: 32 16-bit K elements)
+    static constexpr uint32_t ACOL = MT * 32;
+    static constexpr uint32_t TCOLS = pow2_at_least(ATM ? ACOL + MT * LV * 16 : ACOL);
+    static constexpr int MINB = ATM ? (int)(512 / TCOLS) : 1;   // blocks per SM the TMEM allows
     static_assert(GT % 128 == 0, "whole M tiles");
 };
 
@@ -142,11 +171,11 @@ __device__ __forceinline__ void split1(float v, uint16_t (&out)[3]) {
     }
 }
 
-template <int N, int PREC>
-__global__ void __launch_bounds__(128)
+template <int N, int PREC, bool ATM>
+__global__ void __launch_bounds__(128, TcGeom<N, PREC, ATM>::MINB)
 mma_tc_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld, const float2* filt_pos, const float2* tw,
               int* status, long long wait_cycles) {
-    using GM = TcGeom<N, PREC>;
+    using GM = TcGeom<N, PREC, ATM>;
     using TR = SplitTraits<PREC>;
     using PR = Products<GM::LV>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -207,18 +236,36 @@ mma_tc_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld, const 
             for (int j = 0; j < 16; ++j) m = fmaxf(m, fmaxf(fabsf(x[mt][j].x), fabsf(x[mt][j].y)));
             ex[mt] = (m > 0.f) ? ilogbf(m) + 1 : 0;
             const float sc = ldexpf(1.f, -ex[mt]);
+            if constexpr (ATM) {
+                // row t of the A operand: lane t, 16 columns per split level
+                uint32_t v[3][16];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {   // K elements 8c .. 8c+7: complex 4c .. 4c+3
-                uint32_t pk[4][3];
+                for (int j = 0; j < 16; ++j) {
+                    uint32_t pk[3];
+                    split2<PREC>(x[mt][j].x * sc, x[mt][j].y * sc, pk);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) split2<PREC>(x[mt][4 * c + u].x * sc, x[mt][4 * c + u].y * sc, pk[u]);
+                    for (int l = 0; l < GM::LV; ++l) v[l][j] = pk[l];
+                }
 #pragma unroll
-                for (int l = 0; l < GM::LV; ++l)
-                    *reinterpret_cast<uint4*>(smem_raw + GM::OFF_A + (mt * GM::LV + l) * kATile + km_off(t, 8 * c)) =
-                        make_uint4(pk[0][l], pk[1][l], pk[2][l], pk[3][l]);
+                for (int l = 0; l < GM::LV; ++l) tc_st16(tlane + GM::ACOL + (mt * GM::LV + l) * 16, v[l]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {   // K elements 8c .. 8c+7: complex 4c .. 4c+3
+                    uint32_t pk[4][3];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        split2<PREC>(x[mt][4 * c + u].x * sc, x[mt][4 * c + u].y * sc, pk[u]);
+#pragma unroll
+                    for (int l = 0; l < GM::LV; ++l)
+                        *reinterpret_cast<uint4*>(smem_raw + GM::OFF_A + (mt * GM::LV + l) * kATile +
+                                                  km_off(t, 8 * c)) = make_uint4(pk[0][l], pk[1][l], pk[2][l], pk[3][l]);
+                }
             }
         }
-        fence_proxy_async_smem();
+        if constexpr (ATM)
+            tc_wait_st();
+        else
+            fence_proxy_async_smem();
         tc_fence_before();
         __syncthreads();
         if (t == 0 && ok) {
@@ -229,10 +276,15 @@ mma_tc_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld, const 
                 for (int p = 0; p < PR::COUNT; ++p) {
 #pragma unroll
                     for (int s = 0; s < 2; ++s) {
-                        const uint32_t a = sbase + GM::OFF_A + (mt * GM::LV + PR::a(p)) * kATile + s * 256;
                         const uint32_t b = sbase + GM::OFF_B + ((inv ? 1 : 0) * GM::LV + PR::b(p)) * kBTile + s * 256;
-                        tc_mma(tbase + 32 * mt, tc_sdesc(a, kLBO, kSBO), tc_sdesc(b, kLBO, kSBO), idesc,
-                               (p > 0 || s > 0) ? 1u : 0u);
+                        if constexpr (ATM) {
+                            tc_mma_ts(tbase + 32 * mt, tbase + GM::ACOL + (mt * GM::LV + PR::a(p)) * 16 + 8 * s,
+                                      tc_sdesc(b, kLBO, kSBO), idesc, (p > 0 || s > 0) ? 1u : 0u);
+                        } else {
+                            const uint32_t a = sbase + GM::OFF_A + (mt * GM::LV + PR::a(p)) * kATile + s * 256;
+                            tc_mma(tbase + 32 * mt, tc_sdesc(a, kLBO, kSBO), tc_sdesc(b, kLBO, kSBO), idesc,
+                                   (p > 0 || s > 0) ? 1u : 0u);
+                        }
                     }
                 }
             }
@@ -340,41 +392,48 @@ mma_tc_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld, const 
     if (warp == 0) tc_dealloc(tbase, GM::TCOLS);
 }
 
-template <int N, int PREC>
+template <int N, int PREC, bool ATM>
 cudaError_t launch_tc(const float2* in, float2* out, int64_t n_lines, int64_t ld, const float2* filt_pos,
                       const float2* tw, int* status, long long wait_cycles, cudaStream_t st) {
-    using GM = TcGeom<N, PREC>;
+    using GM = TcGeom<N, PREC, ATM>;
     if (n_lines <= 0) return cudaSuccess;
     static int attr_set[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        e = cudaFuncSetAttribute(mma_tc_kernel<N, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GM::SMEM);
+        e = cudaFuncSetAttribute(mma_tc_kernel<N, PREC, ATM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)GM::SMEM);
         if (e != cudaSuccess) return e;
         attr_set[dev] = 1;
     }
     const int64_t blocks = (n_lines + GM::LPB - 1) / GM::LPB;
-    mma_tc_kernel<N, PREC><<<(unsigned)blocks, 128, GM::SMEM, st>>>(in, out, n_lines, ld, filt_pos, tw, status,
-                                                                    wait_cycles);
+    mma_tc_kernel<N, PREC, ATM><<<(unsigned)blocks, 128, GM::SMEM, st>>>(in, out, n_lines, ld, filt_pos, tw, status,
+                                                                         wait_cycles);
     return cudaGetLastError();
+}
+
+template <int N, int PREC>
+cudaError_t launch_tc_any(bool atm, const float2* in, float2* out, int64_t n_lines, int64_t ld, const float2* filt_pos,
+                          const float2* tw, int* status, long long wait_cycles, cudaStream_t st) {
+    return atm ? launch_tc<N, PREC, true>(in, out, n_lines, ld, filt_pos, tw, status, wait_cycles, st)
+               : launch_tc<N, PREC, false>(in, out, n_lines, ld, filt_pos, tw, status, wait_cycles, st);
 }
 
 }  // namespace
 
-cudaError_t launch_mma_tc_compress(int n, int prec, const float2* in, float2* out, int64_t n_lines, int64_t ld,
-                                   const float2* filt_pos, const float2* tw, int* status, long long wait_cycles,
-                                   cudaStream_t st) {
+cudaError_t launch_mma_tc_compress(int n, int prec, bool a_in_tmem, const float2* in, float2* out, int64_t n_lines,
+                                   int64_t ld, const float2* filt_pos, const float2* tw, int* status,
+                                   long long wait_cycles, cudaStream_t st) {
+    const bool a = a_in_tmem;
     if (n == 4096) {
-        if (prec == kF16x2) return launch_tc<4096, kF16x2>(in, out, n_lines, ld, filt_pos, tw, status, wait_cycles, st);
-        if (prec == kBF16x2)
-            return launch_tc<4096, kBF16x2>(in, out, n_lines, ld, filt_pos, tw, status, wait_cycles, st);
-        if (prec == kBF16x3)
-            return launch_tc<4096, kBF16x3>(in, out, n_lines, ld, filt_pos, tw, status, wait_cycles, st);
+        if (prec == kF16x2) return launch_tc_any<4096, kF16x2>(a, in, out, n_lines, ld, filt_pos, tw, status, wait_cycles, st);
+        if (prec == kBF16x2) return launch_tc_any<4096, kBF16x2>(a, in, out, n_lines, ld, filt_pos, tw, status, wait_cycles, st);
+        if (prec == kBF16x3) return launch_tc_any<4096, kBF16x3>(a, in, out, n_lines, ld, filt_pos, tw, status, wait_cycles, st);
     } else if (n == 256) {
-        if (prec == kF16x2) return launch_tc<256, kF16x2>(in, out, n_lines, ld, filt_pos, tw, status, wait_cycles, st);
-        if (prec == kBF16x2) return launch_tc<256, kBF16x2>(in, out, n_lines, ld, filt_pos, tw, status, wait_cycles, st);
-        if (prec == kBF16x3) return launch_tc<256, kBF16x3>(in, out, n_lines, ld, filt_pos, tw, status, wait_cycles, st);
+        if (prec == kF16x2) return launch_tc_any<256, kF16x2>(a, in, out, n_lines, ld, filt_pos, tw, status, wait_cycles, st);
+        if (prec == kBF16x2) return launch_tc_any<256, kBF16x2>(a, in, out, n_lines, ld, filt_pos, tw, status, wait_cycles, st);
+        if (prec == kBF16x3) return launch_tc_any<256, kBF16x3>(a, in, out, n_lines, ld, filt_pos, tw, status, wait_cycles, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -20,9 +20,11 @@ cudaError_t launch_mma_compress(int n, int prec, const float2 *in, float2 *out, 
 void mma_filter_positions(int n, int32_t *idx);
 // the same on the fifth-generation tensor cores (tcgen05.mma, TMEM
 // accumulators); status / wait_cycles bound its completion waits
-cudaError_t launch_mma_tc_compress(int n, int prec, const float2 *in, float2 *out, int64_t n_lines, int64_t ld,
-                                   const float2 *filt_pos, const float2 *tw, int *status, long long wait_cycles,
-                                   cudaStream_t st);
+// (a_in_tmem: the split data as the A operand in tensor memory, written
+// with tcgen05.st; else in shared-memory tiles)
+cudaError_t launch_mma_tc_compress(int n, int prec, bool a_in_tmem, const float2 *in, float2 *out, int64_t n_lines,
+                                   int64_t ld, const float2 *filt_pos, const float2 *tw, int *status,
+                                   long long wait_cycles, cudaStream_t st);
 // full Range-Doppler processing (RCMC and the range-dependent azimuth filter)
 const char *rd_az_schedule(int n);
 cudaError_t launch_az_compress_rd(int n, const float2 *in, float2 *out, int64_t n_lines, const float2 *tw,

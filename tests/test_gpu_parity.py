@@ -577,7 +577,7 @@ def test_empty_inputs(sar):
 PREC_GATES = {"FP16X2": 2e-5, "BF16X3": 2e-5, "BF16X2": 2e-4}
 
 
-@pytest.mark.parametrize("engine", [0, 1], ids=["tcgen05", "mma_sync"])
+@pytest.mark.parametrize("engine", [0, 2, 1], ids=["tcgen05_tmem_a", "tcgen05_smem_a", "mma_sync"])
 @pytest.mark.parametrize("prec", ["FP16X2", "BF16X2", "BF16X3"])
 @pytest.mark.parametrize("make", [sarsim.scene_256, sarsim.scene_4096], ids=["256", "4096"])
 def test_split_precision_vs_oracle(sar, orc, prec, make, engine):
@@ -626,7 +626,7 @@ def test_split_precision_refusals(sar):
         sar.sar_plan_create(1024, 1024, x, x, precision=9)
     assert e.value.status == sar.SAR_ERR_INVALID_ARG
     with pytest.raises(sar.SarError) as e:
-        sar.sar_set_split_engine(2)
+        sar.sar_set_split_engine(3)
     assert e.value.status == sar.SAR_ERR_INVALID_ARG
 
 
