@@ -10,7 +10,8 @@
 //     Y = X F^T          (128 groups x 32) = (128 x 32)(32 x 32)
 // one tcgen05.mma shape with M = 128 (groups), N = 32, K = 32 (two K = 16
 // steps).  X is split per group into half-precision parts
-// x = 2^e (x_hi + x_lo [+ x_mid]) after scaling by a power of two to |x| < 1,
+// x = 2^e (x_hi + x_lo [+ x_mid]), for FP16 after scaling each group by a
+// power of two to |x| < 1 (BF16 has FP32's exponent range: e = 0),
 // F into f_hi + f_lo [+ f_mid], and the products
 // hi*hi + hi*lo + lo*hi (BF16 x3: hh + hm + mh + hl + lh + mm) accumulate in
 // FP32 in TMEM.  Row m of the accumulator is TMEM lane m, so after the MMA
@@ -228,14 +229,21 @@ mma_tc_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld, const 
 
     // y = F x (or conj(F) x) for the MT groups of this thread, in place.
     auto dft_round = [&](float2 (&x)[GM::MT][16], bool inv) {
+        // FP16 parts need each group scaled into range (a power of two, exact);
+        // BF16 has FP32's exponent range and takes the values as they are
+        constexpr bool SCALE = PREC == kF16x2;
         int ex[GM::MT];
 #pragma unroll
         for (int mt = 0; mt < GM::MT; ++mt) {
-            float m = 0.f;
+            float sc = 1.f;
+            ex[mt] = 0;
+            if constexpr (SCALE) {
+                float m = 0.f;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) m = fmaxf(m, fmaxf(fabsf(x[mt][j].x), fabsf(x[mt][j].y)));
-            ex[mt] = (m > 0.f) ? ilogbf(m) + 1 : 0;
-            const float sc = ldexpf(1.f, -ex[mt]);
+                for (int j = 0; j < 16; ++j) m = fmaxf(m, fmaxf(fabsf(x[mt][j].x), fabsf(x[mt][j].y)));
+                ex[mt] = (m > 0.f) ? ilogbf(m) + 1 : 0;
+                sc = ldexpf(1.f, -ex[mt]);
+            }
             if constexpr (ATM) {
                 // row t of the A operand: lane t, 16 columns per split level
                 uint32_t v[3][16];
@@ -299,9 +307,14 @@ mma_tc_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld, const 
         for (int mt = 0; mt < GM::MT; ++mt) {
             float d[32];
             tc_ld32(tlane + 32 * mt, d);
-            const float sc = ldexpf(1.f, ex[mt]);
+            if constexpr (SCALE) {
+                const float sc = ldexpf(1.f, ex[mt]);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) x[mt][j] = make_float2(d[2 * j] * sc, d[2 * j + 1] * sc);
+                for (int j = 0; j < 16; ++j) x[mt][j] = make_float2(d[2 * j] * sc, d[2 * j + 1] * sc);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) x[mt][j] = make_float2(d[2 * j], d[2 * j + 1]);
+            }
         }
         tc_fence_before();
     };
