@@ -521,18 +521,21 @@ def long_lines_bench(sar, stream, peak, reps: int = 10) -> dict:
 
 def any_length_bench(sar, dev, stream, peak, reps: int = 20) -> dict:
     """The fused range pass over about 384 MiB of lines of n samples for
-    lengths that are not powers of two (engine length L = next pow2 >=
-    2n - 1), beside the power-of-two lengths around them; GB/s over 16 B per
+    lengths that are not powers of two -- the mixed-radix engine at n itself
+    where n's prime factors are 2, 3, 5, 7 (1000, 3000, 5000, 8000), the
+    zero-padded convolution at L = next pow2 >= 2n - 1 otherwise (1009,
+    3001) -- beside the power-of-two lengths around them; GB/s over 16 B per
     sample of n (one read and one write)."""
     import torch
     out = {}
-    for n in (1000, 1024, 3000, 4096, 5000, 8000, 8192):
+    for n in (1000, 1009, 1024, 3000, 3001, 4096, 5000, 8000, 8192):
         n_lines = 1 << max(8, ((384 << 20) // (8 * n) - 1).bit_length())
         data = torch.zeros((n_lines, n), dtype=torch.complex64, device=dev)
         Hr = torch.ones(n, dtype=torch.complex64, device=dev)
         Ha = torch.ones(n_lines, dtype=torch.complex64, device=dev)
         plan = sar.sar_plan_create(n, n_lines, Hr, Ha)
-        L = sar.sar_plan_get_schedules(plan)[0]["n"]
+        sched = sar.sar_plan_get_schedules(plan)[0]
+        L = sched["n"]
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         times = []
         for i in range(reps + 3):
@@ -545,7 +548,8 @@ def any_length_bench(sar, dev, stream, peak, reps: int = 20) -> dict:
         times.sort()
         ms = times[len(times) // 2]
         gbs = 16.0 * n * n_lines / (ms * 1e-3) / 1e9
-        out[str(n)] = {"engine_length": L, "lines": n_lines, "ms": ms, "gb_s": gbs, "frac_hbm": gbs / peak}
+        out[str(n)] = {"engine_length": L, "schedule": sched["name"], "lines": n_lines, "ms": ms, "gb_s": gbs,
+                       "frac_hbm": gbs / peak}
         plan.destroy()
         # the DFT alone at the same length (Bluestein when n is not a power of two)
         times = []

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/sar.h"
+#include "mixed_radix.h"
 #include "registry.h"
 #include "tables.h"
 
@@ -53,8 +54,10 @@ sar_status check_length(int64_t n, const char *what) {
 }
 
 // A plan's line length: a power of two in [256, 131072] (the line engine at
-// that length), or any other length in [2, 8192] (the zero-padded linear
-// convolution at L = max(256, next power of two >= 2n - 1), wrap_line.cu).
+// that length), or any other length in [2, 8192]: the mixed-radix engine at
+// the length itself when its prime factors are 2, 3, 5, 7 (mixed_radix.cu),
+// else the zero-padded linear convolution at L = max(256, next power of two
+// >= 2n - 1) (wrap_line.cu).
 bool native_length(int64_t n) { return is_pow2(n) && n >= 256 && n <= 131072; }
 
 sar_status check_plan_length(int64_t n, const char *what) {
@@ -302,12 +305,14 @@ sar_status sar_plan_create_ex(int64_t n_range, int64_t n_az, const sar_filters *
     const bool want_fold = !(filters->flags & SAR_PLAN_UNFOLDED_CORNER_TURN) && prec == SAR_PREC_FP32 && !wrap_r;
     const SchedDesc *dr = range_schedule ? sar::find_schedule(range_schedule) : nullptr;
     if (wrap_r) {
-        dr = sar::wrap_schedule((int)wrap_length(n_range));
+        dr = sar::mixed_length((int)n_range) ? sar::mixed_schedule((int)n_range)
+                                             : sar::wrap_schedule((int)wrap_length(n_range));
     } else if (!range_schedule) {
         dr = want_fold ? sar::default_ct_schedule((int)n_range) : nullptr;
         if (!dr || n_az % dr->ct_lines) dr = sar::default_schedule((int)n_range);
     }
-    const SchedDesc *da = wrap_a ? sar::wrap_schedule((int)wrap_length(n_az))
+    const SchedDesc *da = wrap_a ? (sar::mixed_length((int)n_az) ? sar::mixed_schedule((int)n_az)
+                                                                  : sar::wrap_schedule((int)wrap_length(n_az)))
                                  : az_schedule ? sar::find_schedule(az_schedule) : sar::default_schedule((int)n_az);
     if (range_schedule && (!dr || dr->n != n_range))
         return fail(SAR_ERR_INVALID_ARG, "range schedule '%s' is unknown or not for n_range", range_schedule);

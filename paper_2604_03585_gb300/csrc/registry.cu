@@ -3,6 +3,7 @@
 
 #include <mutex>
 
+#include "mixed_radix.h"
 #include "registry.h"
 
 namespace sar {
@@ -89,6 +90,10 @@ void set_preferred_ct_schedule(const SchedDesc *d) {
 }
 
 void filter_slot_to_k(const SchedDesc &d, int32_t *idx) {
+    if (d.mixed) {
+        mixed_positions(d.n, idx);
+        return;
+    }
     const int C = d.cluster > 1 ? d.cluster : 1;
     const int N = d.n / C, E = d.e, T = N / E, RL = d.rl;   // N: the per-block engine's length
     const int S1 = N / d.r1;

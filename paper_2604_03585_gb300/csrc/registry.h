@@ -50,6 +50,8 @@ struct SchedDesc {
                             // e, r1..r3, rl, threads and smem_bytes then describe each block's
                             // M = n / cluster point engine, and the twiddle table is the M-point
                             // engine's followed by W_N^j for j < n
+    int mixed;              // 1: the mixed-radix engine of a 7-smooth length (mixed_radix.h): r1..r3
+                            // are its first radices, e is 0, the filter is in position order
 };
 
 // All compiled schedules (one table per translation unit).

@@ -1,5 +1,6 @@
 // Plan-time tables: FP64 twiddle and chirp phases rounded to FP32, and the
 // matched filter permuted into the fused kernel's register order.
+#include "mixed_radix.h"
 #include "tables.h"
 
 namespace sar {
@@ -185,6 +186,7 @@ cudaError_t build_natural_filter(const float2 *H, float2 *dst, int n, cudaStream
 }
 
 cudaError_t build_twiddles(const SchedDesc &d, float2 *tw, cudaStream_t st) {
+    if (d.mixed) return build_mixed_twiddles(d.n, tw, st);
     const int M = d.cluster > 1 ? d.n / d.cluster : d.n;   // the per-block engine's length
     const int S1 = M / d.r1;
     int total = d.r1 * S1;

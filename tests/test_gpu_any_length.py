@@ -39,11 +39,23 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex64)).cuda()
 
 
-# n, lines: every engine length L = max(256, next pow2 >= 2n - 1) from 256 to
-# 16384, the smallest and largest n of several of them, and n = 2
-@pytest.mark.parametrize("n,lines", [(2, 5), (3, 7), (100, 9), (128, 9), (129, 9), (255, 9), (257, 6), (500, 6),
-                                     (1000, 5), (1023, 5), (1500, 4), (2049, 3), (3000, 3), (4095, 3), (5000, 2),
-                                     (8191, 2)])
+def seven_smooth(n):
+    for p in (2, 3, 5, 7):
+        while n % p == 0:
+            n //= p
+    return n == 1
+
+
+# n, lines: lengths whose prime factors are 2, 3, 5, 7 (the mixed-radix
+# engine at the length itself: one to four passes, radices 2 ... 32, prime
+# factors 3, 5, 7 alone and combined) and other lengths (the zero-padded
+# convolution at every engine length L = max(256, next pow2 >= 2n - 1) from
+# 256 to 16384), the smallest and largest n of several of them, and n = 2
+@pytest.mark.parametrize("n,lines", [(2, 5), (3, 7), (6, 5), (7, 5), (12, 5), (15, 4), (49, 4), (100, 9),
+                                     (128, 9), (129, 9), (255, 9), (257, 6), (343, 4), (500, 6), (1000, 5),
+                                     (1023, 5), (1029, 4), (1500, 4), (2049, 3), (2401, 2), (3000, 3), (3125, 2),
+                                     (4095, 3), (4374, 2), (5000, 2), (6000, 2), (6561, 2), (7000, 2), (7776, 2),
+                                     (8000, 2), (8191, 2)])
 def test_line_compression_any_length(sar, orc, n, lines):
     x = noise(31 + n, lines, n)
     nc = max(1, n // 4)
@@ -65,12 +77,16 @@ def test_line_compression_any_length(sar, orc, n, lines):
     torch.cuda.synchronize()
     got2 = out.cpu().numpy()
     assert np.array_equal(xd.cpu().numpy(), x.astype(np.complex64))
-    L = sar.sar_plan_get_schedules(plan)[0]["n"]
+    sched = sar.sar_plan_get_schedules(plan)[0]
+    L = sched["n"]
     plan.destroy()
     plan2.destroy()
     e1, e2 = M.rel_l2(got, ref), M.rel_l2(got2, ref2)
-    print(f"\nANY n={n} (L={L}): matched {e1:.2e}, random H {e2:.2e}")
-    assert L == max(256, 1 << (2 * n - 2).bit_length())
+    print(f"\nANY n={n} ({sched['name']}, L={L}): matched {e1:.2e}, random H {e2:.2e}")
+    if seven_smooth(n):
+        assert L == n and "mixed" in sched["name"]
+    else:
+        assert L == max(256, 1 << (2 * n - 2).bit_length())
     assert e1 < LINE_TOL and e2 < LINE_TOL
 
 
@@ -109,15 +125,19 @@ def test_scene_any_length_vs_oracle(sar, orc, n_az, n_range):
 
 
 def test_schedules_of_any_length_plans(sar):
-    a, b = dev(np.ones(1000)), dev(np.ones(300))
-    plan = sar.sar_plan_create(1000, 300, a, b)
+    a, b = dev(np.ones(1009)), dev(np.ones(300))
+    plan = sar.sar_plan_create(1009, 300, a, b)       # 1009 is prime: zero-padded convolution
     r, z = sar.sar_plan_get_schedules(plan)
     assert r["n"] == 2048 and r["name"].startswith("wrap_")
-    assert z["n"] == 1024 and z["name"].startswith("wrap_")
+    assert z["n"] == 300 and z["name"] == "n300_mixed_r20x15"   # 300 = 20 * 15: mixed radix, two passes
     assert not sar.sar_plan_folds_corner_turn(plan)
     plan.destroy()
-    # wrap schedules are not part of the enumeration (and so never autotuned)
-    assert not [d for d in sar.schedules() if d["name"].startswith("wrap_")]
+    plan = sar.sar_plan_create(300, 1009, b, a)
+    r, z = sar.sar_plan_get_schedules(plan)
+    assert r["name"] == "n300_mixed_r20x15" and z["name"].startswith("wrap_")
+    plan.destroy()
+    # wrap and mixed-radix schedules are not part of the enumeration (never autotuned)
+    assert not [d for d in sar.schedules() if d["name"].startswith("wrap_") or "mixed" in d["name"]]
 
 
 def test_any_length_refusals(sar):
