@@ -19,11 +19,15 @@
 // each group's work is dispatched on it to a routine compiled for that
 // radix, whose register array is indexed only by compile-time constants.  An
 // R-point DFT is a recursive decimation in frequency over its smallest factor
-// (radix-4, then 2, 3, 5, 7 butterflies by their definition), with
-// compile-time twiddles from the same series as the power-of-two engine.
+// (radix-4, then 2, 3, 5, 7 butterflies; the odd ones through the symmetry
+// of their roots), with compile-time twiddles from the same series as the
+// power-of-two engine.
 //
-// One block of 256 threads per line; the line lives in shared memory between
-// passes, padded with one slot per 32 elements.
+// Blocks of 256 threads: T threads per line (a power of two covering about
+// half the largest group count of a pass), 256 / T lines per block; a line
+// lives in shared memory between passes, padded with one slot per 32
+// elements.  Group indexes are split by a multiply-high with ceil(2^32 / S)
+// instead of an integer division (exact for every index below 2^19).
 #include <map>
 #include <mutex>
 #include <string>
@@ -45,6 +49,9 @@ constexpr int kRadices[] = {32, 25, 20, 16, 15, 14, 12, 10, 9, 8, 7, 6, 5, 4, 3,
 struct MixedGeom {
     int n, P;
     int R[kMaxPasses], S[kMaxPasses], tw_off[kMaxPasses];
+    uint32_t M[kMaxPasses];   // ceil(2^32 / S): g / S == umulhi(g, M) for every g < 8192 and 2 <= S <= 8192
+                              // (checked exhaustively); 0 for S == 1
+    int T;                    // threads per line; kMixedThreads / T lines per block
 };
 
 __device__ __forceinline__ int mpad(int p) { return p + (p >> 5); }
@@ -58,19 +65,63 @@ __host__ __device__ constexpr int mpos(int L, int k) {
     return L == 1 ? 0 : ((k % small_factor(L)) * (L / small_factor(L)) + mpos(L / small_factor(L), k / small_factor(L)));
 }
 
-// p-point DFT of a[0..p-1] by its definition, constant twiddles
-template <int p, int k, bool INV, int... M>
-__device__ __forceinline__ float2 dft_out(const float2 (&a)[p], std::integer_sequence<int, M...>) {
-    float2 s = a[0];
-    ((s = (M == 0) ? s : cadd(s, twiddle_ct<p, (M * k) % p, INV>(a[M]))), ...);
-    return s;
+// p-point DFT of a[0..p-1] for an odd prime p, by the symmetry of the
+// roots: with a_k = x_k + x_{p-k} and b_k = x_k - x_{p-k} (k = 1 .. h,
+// h = (p - 1) / 2),
+//   y_0 = x_0 + sum_k a_k,
+//   y_j = t_j -+ i u_j,  y_{p-j} = t_j +- i u_j   (j = 1 .. h; upper signs
+//   forward), t_j = x_0 + sum_k cos(2 pi j k / p) a_k,
+//   u_j = sum_k sin(2 pi j k / p) b_k,
+// real constants only: about 5 instructions per output at p = 5 instead of
+// the 16 of the definition's p - 1 complex products per output.
+template <int p, int j, int... K>
+__device__ __forceinline__ float2 odd_t(float2 x0, const float2 (&av)[p], std::integer_sequence<int, K...>) {
+    float2 t = x0;
+    ((t = make_float2(fmaf((float)ct::cos2pi((K + 1) * j, p), av[K + 1].x, t.x),
+                      fmaf((float)ct::cos2pi((K + 1) * j, p), av[K + 1].y, t.y))),
+     ...);
+    return t;
 }
-template <int p, bool INV, int... K>
-__device__ __forceinline__ void dft_small(float2 (&a)[p], std::integer_sequence<int, K...>) {
-    float2 b[p];
-    ((b[K] = dft_out<p, K, INV>(a, std::make_integer_sequence<int, p>{})), ...);
+template <int p, int j, int... K>
+__device__ __forceinline__ float2 odd_u(const float2 (&bv)[p], std::integer_sequence<int, K...>) {
+    float2 u = make_float2(0.f, 0.f);
+    ((u = make_float2(fmaf((float)ct::sin2pi((K + 1) * j, p), bv[K + 1].x, u.x),
+                      fmaf((float)ct::sin2pi((K + 1) * j, p), bv[K + 1].y, u.y))),
+     ...);
+    return u;
+}
+template <int p, bool INV, int... J>
+__device__ __forceinline__ void dft_odd_outputs(float2 (&a)[p], float2 x0, const float2 (&av)[p],
+                                                const float2 (&bv)[p], std::integer_sequence<int, J...>) {
+    constexpr int h = (p - 1) / 2;
+    float2 y[p];
+    (([&] {
+         constexpr int j = J + 1;
+         const float2 t = odd_t<p, j>(x0, av, std::make_integer_sequence<int, h>{});
+         const float2 u = odd_u<p, j>(bv, std::make_integer_sequence<int, h>{});
+         // -i u = (u.y, -u.x); +i u = (-u.y, u.x)
+         const float2 mi = make_float2(u.y, -u.x);
+         y[j] = INV ? csub(t, mi) : cadd(t, mi);
+         y[p - j] = INV ? cadd(t, mi) : csub(t, mi);
+     }()),
+     ...);
 #pragma unroll
-    for (int k = 0; k < p; ++k) a[k] = b[k];
+    for (int k = 1; k < p; ++k) a[k] = y[k];
+}
+template <int p, bool INV>
+__device__ __forceinline__ void dft_odd(float2 (&a)[p]) {
+    constexpr int h = (p - 1) / 2;
+    float2 av[p], bv[p];
+    float2 y0 = a[0];
+#pragma unroll
+    for (int k = 1; k <= h; ++k) {
+        av[k] = cadd(a[k], a[p - k]);
+        bv[k] = csub(a[k], a[p - k]);
+        y0 = cadd(y0, av[k]);
+    }
+    const float2 x0 = a[0];
+    dft_odd_outputs<p, INV>(a, x0, av, bv, std::make_integer_sequence<int, h>{});
+    a[0] = y0;
 }
 
 template <int R, int L, int OFF, bool INV, int J, int... K>
@@ -99,7 +150,7 @@ __device__ __forceinline__ void mlevel_one(float2 (&v)[R]) {
         a[0] = cadd(t, a[1]);
         a[1] = csub(t, a[1]);
     } else {
-        dft_small<p, INV>(a, std::make_integer_sequence<int, p>{});
+        dft_odd<p, INV>(a);
     }
     mlevel_store<R, L, OFF, INV, J>(v, a, std::make_integer_sequence<int, p>{});
 }
@@ -146,9 +197,10 @@ enum MMode { kFirst, kMid, kLast, kInvMid, kInvFirst };
 // global when P == 1); kInvMid smem -> conj twiddle -> IDFT -> smem; kInvFirst
 // smem -> conj twiddle -> IDFT -> global.
 template <int R, int MODE, bool SINGLE>
-__device__ __forceinline__ void mgroup(int g, int S, const float2* src, float2* dst, float2* sm, const float2* twi,
-                                       const float2* filt) {
-    const int lo = g % S, base = (g / S) * R * S + lo;
+__device__ __forceinline__ void mgroup(int g, int S, uint32_t M, const float2* src, float2* dst, float2* sm,
+                                       const float2* twi, const float2* filt) {
+    const int q = M ? (int)__umulhi((uint32_t)g, M) : g;   // M == 0: S == 1
+    const int lo = g - q * S, base = q * R * S + lo;
     float2 v[R];
     const bool from_global = MODE == kFirst || (MODE == kLast && SINGLE);
 #pragma unroll
@@ -179,12 +231,12 @@ __device__ __forceinline__ void mgroup(int g, int S, const float2* src, float2* 
 }
 
 template <int MODE, bool SINGLE>
-__device__ __forceinline__ void mpass(int R, int S, int n, const float2* src, float2* dst, float2* sm,
-                                      const float2* twi, const float2* filt) {
+__device__ __forceinline__ void mpass(int R, int S, uint32_t M, int n, int t, int T, const float2* src, float2* dst,
+                                      float2* sm, const float2* twi, const float2* filt) {
     const int ng = n / R;
-#define SAR_MIXED_CASE(RR)                                                                              \
-    case RR:                                                                                            \
-        for (int g = threadIdx.x; g < ng; g += kMixedThreads) mgroup<RR, MODE, SINGLE>(g, S, src, dst, sm, twi, filt); \
+#define SAR_MIXED_CASE(RR)                                                                       \
+    case RR:                                                                                     \
+        for (int g = t; g < ng; g += T) mgroup<RR, MODE, SINGLE>(g, S, M, src, dst, sm, twi, filt); \
         break;
     switch (R) {
         SAR_MIXED_CASE(2)
@@ -208,32 +260,36 @@ __device__ __forceinline__ void mpass(int R, int S, int n, const float2* src, fl
 #undef SAR_MIXED_CASE
 }
 
+// Lines of T threads each, kMixedThreads / T lines per block (lines past the
+// end still take part in the block's barriers).
 __global__ void __launch_bounds__(kMixedThreads)
 fused_mixed_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld, const float2* filt, const float2* tw,
                    MixedGeom geo) {
-    extern __shared__ float2 sm[];
-    const int64_t line = blockIdx.x;
-    if (line >= n_lines) return;
-    const float2* src = in + line * ld;
-    float2* dst = out + line * ld;
+    extern __shared__ float2 smem_mixed[];
+    const int T = geo.T, lib = threadIdx.x / T, t = threadIdx.x % T;
+    const int64_t line = (int64_t)blockIdx.x * (kMixedThreads / T) + lib;
+    const bool live = line < n_lines;
     const int n = geo.n, P = geo.P;
+    float2* sm = smem_mixed + lib * (n + (n >> 5) + 1);
+    const float2* src = in + (live ? line : 0) * ld;
+    float2* dst = out + (live ? line : 0) * ld;
     if (P == 1) {
-        mpass<kLast, true>(geo.R[0], 1, n, src, dst, sm, tw, filt);
+        if (live) mpass<kLast, true>(geo.R[0], 1, 0u, n, t, T, src, dst, sm, tw, filt);
         return;
     }
-    mpass<kFirst, false>(geo.R[0], geo.S[0], n, src, dst, sm, tw + geo.tw_off[0], filt);
+    if (live) mpass<kFirst, false>(geo.R[0], geo.S[0], geo.M[0], n, t, T, src, dst, sm, tw + geo.tw_off[0], filt);
     __syncthreads();
     for (int i = 1; i < P - 1; ++i) {
-        mpass<kMid, false>(geo.R[i], geo.S[i], n, src, dst, sm, tw + geo.tw_off[i], filt);
+        if (live) mpass<kMid, false>(geo.R[i], geo.S[i], geo.M[i], n, t, T, src, dst, sm, tw + geo.tw_off[i], filt);
         __syncthreads();
     }
-    mpass<kLast, false>(geo.R[P - 1], 1, n, src, dst, sm, tw, filt);
+    if (live) mpass<kLast, false>(geo.R[P - 1], 1, 0u, n, t, T, src, dst, sm, tw, filt);
     __syncthreads();
     for (int i = P - 2; i >= 1; --i) {
-        mpass<kInvMid, false>(geo.R[i], geo.S[i], n, src, dst, sm, tw + geo.tw_off[i], filt);
+        if (live) mpass<kInvMid, false>(geo.R[i], geo.S[i], geo.M[i], n, t, T, src, dst, sm, tw + geo.tw_off[i], filt);
         __syncthreads();
     }
-    mpass<kInvFirst, false>(geo.R[0], geo.S[0], n, src, dst, sm, tw + geo.tw_off[0], filt);
+    if (live) mpass<kInvFirst, false>(geo.R[0], geo.S[0], geo.M[0], n, t, T, src, dst, sm, tw + geo.tw_off[0], filt);
 }
 
 // tw[off_i + r S_i + lo] = exp(-2 pi i lo r / (R_i S_i)), FP64 phases rounded
@@ -256,12 +312,14 @@ bool seven_smooth(int n) {
     return n == 1;
 }
 
-// fewest radices from kRadices multiplying to n; ties: the largest smallest
-// radix (balanced passes); the radices in descending order
+// fewest radices from kRadices multiplying to n; ties: the smallest largest
+// radix, then the largest smallest one (balanced passes: similar group counts
+// per pass, fewer registers per group); the radices in descending order
 void search(int n, int start, std::vector<int>& cur, std::vector<int>& best) {
     if (n == 1) {
         if (best.empty() || cur.size() < best.size() ||
-            (cur.size() == best.size() && cur.back() > best.back()))
+            (cur.size() == best.size() &&
+             (cur.front() < best.front() || (cur.front() == best.front() && cur.back() > best.back()))))
             best = cur;
         return;
     }
@@ -282,14 +340,20 @@ bool geometry(int n, MixedGeom& g) {
     if (best.empty()) return false;
     g.n = n;
     g.P = (int)best.size();
-    int rest = n, off = 0;
+    int rest = n, off = 0, most = 1;
     for (int i = 0; i < kMaxPasses; ++i) {
         g.R[i] = i < g.P ? best[i] : 1;
         if (i < g.P) rest /= g.R[i];
         g.S[i] = i < g.P ? rest : 1;
+        g.M[i] = g.S[i] > 1 ? (uint32_t)((((uint64_t)1 << 32) + (uint64_t)g.S[i] - 1) / (uint64_t)g.S[i]) : 0u;
         g.tw_off[i] = off;
         if (i < g.P - 1) off += g.R[i] * g.S[i];
+        if (i < g.P && n / g.R[i] > most) most = n / g.R[i];
     }
+    // threads per line: a power of two covering about half the largest group
+    // count of a pass (one or two groups per thread), 32 ... kMixedThreads
+    g.T = 32;
+    while (g.T < kMixedThreads && 2 * g.T < most) g.T <<= 1;
     return true;
 }
 
@@ -299,19 +363,24 @@ int twiddle_elems(const MixedGeom& g) {
     return e > 0 ? e : 1;
 }
 
-int smem_bytes(int n) { return (n + (n >> 5) + 1) * (int)sizeof(float2); }
+int lines_per_block(const MixedGeom& g) { return kMixedThreads / g.T; }
+int smem_bytes(const MixedGeom& g) { return lines_per_block(g) * (g.n + (g.n >> 5) + 1) * (int)sizeof(float2); }
 
 cudaError_t launch_mixed(const float2* in, float2* out, int64_t n_lines, int64_t ld, int valid, const float2* filt,
                          const float2* tw, const FusedCtl&, cudaStream_t st) {
     if (n_lines <= 0) return cudaSuccess;
     MixedGeom g{};
     if (!geometry(valid, g)) return cudaErrorInvalidValue;
-    fused_mixed_kernel<<<(unsigned)n_lines, kMixedThreads, smem_bytes(valid), st>>>(in, out, n_lines, ld, filt, tw, g);
+    const int lpb = lines_per_block(g);
+    fused_mixed_kernel<<<(unsigned)((n_lines + lpb - 1) / lpb), kMixedThreads, smem_bytes(g), st>>>(in, out, n_lines,
+                                                                                                    ld, filt, tw, g);
     return cudaGetLastError();
 }
 
+// the largest block shared memory of any length: eight lines of at most
+// 1024 samples or one of 8192, about 68 KiB
 cudaError_t prepare_mixed() {
-    return cudaFuncSetAttribute(fused_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(8192));
+    return cudaFuncSetAttribute(fused_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 72 * 1024);
 }
 
 struct Entry {
@@ -337,9 +406,9 @@ const SchedDesc* mixed_schedule(int n) {
     Entry* e = new Entry;
     e->name = "n" + std::to_string(n) + "_mixed_r";
     for (int i = 0; i < g.P; ++i) e->name += (i ? "x" : "") + std::to_string(g.R[i]);
-    e->desc = SchedDesc{e->name.c_str(), n, 0, g.R[0], g.P > 1 ? g.R[1] : 1, g.P > 2 ? g.R[2] : 1, 1,
-                        kMixedThreads, smem_bytes(n), twiddle_elems(g), g.R[g.P - 1], 0, &launch_mixed, nullptr,
-                        &prepare_mixed, nullptr, 0, nullptr, 0};
+    e->desc = SchedDesc{e->name.c_str(), n, 0, g.R[0], g.P > 1 ? g.R[1] : 1, g.P > 2 ? g.R[2] : 1,
+                        lines_per_block(g), kMixedThreads, smem_bytes(g), twiddle_elems(g), g.R[g.P - 1], 0,
+                        &launch_mixed, nullptr, &prepare_mixed, nullptr, 0, nullptr, 0};
     e->desc.mixed = 1;
     g_descs[n] = e;
     return &e->desc;
