@@ -111,10 +111,17 @@ typedef struct {
 /* Create a plan for an n_az x n_range scene (Sec. IV-A, the N_a x N_r data
  * matrix).  n_range and n_az: powers of two in [256, 131072] (above 16384 on
  * thread-block clusters, without the folded corner turn), or any other length
- * in [2, 8192]: such lines get the exact length-n compression
- * IFFT_n(FFT_n(x) . H) through a zero-padded linear convolution at the
- * power-of-two length L >= 2n - 1 (filter FFT_L(IFFT_n(H)) designed in FP64 at
- * plan time), one fused launch per pass as for powers of two; the unfused
+ * in [2, 8192], which gets the exact length-n compression
+ * IFFT_n(FFT_n(x) . H):
+ *   - lengths whose prime factors are 2, 3, 5 and 7 only (1000, 3000, 5000,
+ *     ..., and powers of two below 256) and that split into at most four
+ *     radices of 2 ... 16, 20, 25, 32 run the mixed-radix engine at n itself
+ *     (twiddles and filter order designed in FP64 at plan time);
+ *   - every other length (a prime factor above 7, e.g. 1009, or 7203 =
+ *     3 * 7^4) runs a zero-padded linear convolution at the power-of-two
+ *     length L >= 2n - 1 (filter FFT_L(IFFT_n(H)) designed in FP64 at plan
+ *     time);
+ * one fused launch per pass either way, as for powers of two.  The unfused
  * pipeline and split precision need powers of two.  Allocates the
  * plan's device tables on the current device, builds them (FP64 twiddle
  * phases rounded to FP32) and synchronises the device once; not for the hot
