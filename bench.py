@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--azimuth-schedule", default=None, help="schedule of the azimuth pass (default: autotuned)")
     ap.add_argument("--no-autotune", action="store_true", help="use the compiled-in preferred schedules")
     ap.add_argument("--no-extras", action="store_true", help="skip the ragged-batch and serving measurements")
+    ap.add_argument("--ragged-strips", type=int, default=64,
+                    help="strips of the ragged-batch section (64: the configuration; fewer for a small ncu case)")
     ap.add_argument("--extras", default=",".join(EXTRAS),
                     help="comma-separated extra measurements to run after the headline step")
     args = ap.parse_args()
@@ -615,10 +617,10 @@ def rda_full_bench(sar, dev, stream, work, image, reps: int = 50) -> dict:
 # ragged batch: 64 strips of mixed sizes in one CUDA-graph launch
 # ---------------------------------------------------------------------------
 
-def ragged_batch_bench(sar, roofline, dev, stream, peak, reps: int = 10) -> dict:
+def ragged_batch_bench(sar, roofline, dev, stream, peak, reps: int = 10, strips_n: int = 64) -> dict:
     import torch
     import sarsim
-    specs = sarsim.ragged_batch_specs(4, 64)
+    specs = sarsim.ragged_batch_specs(4, strips_n)
     hr, ha, strips, keep = {}, {}, [], []
     with torch.cuda.stream(stream):
         for sp in specs:
@@ -696,7 +698,7 @@ def ragged_batch_bench(sar, roofline, dev, stream, peak, reps: int = 10) -> dict
             "azimuth_classes": info["azimuth_classes"], "algorithmic_bytes": alg,
             "achieved_GBps": gbs, "frac_of_hbm_peak": gbs / peak,
             "bytes_note": "32 B per unpadded sample (range pass with the corner turn folded in, azimuth pass)",
-            "inputs": "64 seeded strips (sarsim.ragged_batch_specs(4, 64)), echoes by the device simulator",
+            "inputs": f"{len(specs)} seeded strips (sarsim.ragged_batch_specs(4, {len(specs)})), echoes by the device simulator",
             "multi_kernel": {"ms_per_graph_launch": mms, "kernels_per_graph": minfo["kernels_per_run"],
                              "algorithmic_bytes": alg48, "achieved_GBps": alg48 / (mms * 1e-3) / 1e9,
                              "frac_of_hbm_peak": alg48 / (mms * 1e-3) / 1e9 / peak,
@@ -1000,7 +1002,7 @@ def main():
     if "any_length" in wanted:
         extras["any_length"] = any_length_bench(sar, dev, stream, peak)
     if "ragged_batch" in wanted:
-        extras["ragged_batch"] = ragged_batch_bench(sar, roofline, dev, stream, peak)
+        extras["ragged_batch"] = ragged_batch_bench(sar, roofline, dev, stream, peak, strips_n=args.ragged_strips)
     if "serving" in wanted:
         extras["serving"] = serving_bench(sar, dev, stream)
 
