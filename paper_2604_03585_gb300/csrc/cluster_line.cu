@@ -55,8 +55,8 @@ __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.w
 
 // Step 1: C-point DFTs over n1 and the twiddle W_N^{n2 k1}, pushed to block
 // k1 at position n2 (PADDED: at the line engine's padded shared-memory slot of
-// n2), one n2 at a time (C values live).  roots[j] = W_N^j,
-// j < N.  The block announces itself on the cluster barrier at once and waits
+// n2), one n2 at a time (C values live).  roots[k1 M + n2] = W_N^{k1 n2}
+// (one contiguous row per k1).  The block announces itself on the cluster barrier at once and waits
 // for the others just before its first remote store.
 template <class SC, int C, bool RAGGED, bool CONJ_IN, bool PADDED = false>
 __device__ __forceinline__ void cluster_first_stage(const float2* src, int valid, const float2* roots, int t,
@@ -77,7 +77,7 @@ __device__ __forceinline__ void cluster_first_stage(const float2* src, int valid
         }
         dft_reg<C, false>(a);
 #pragma unroll
-        for (int k1 = 1; k1 < C; ++k1) a[k1] = cmul(a[k1], roots[n2 * k1]);
+        for (int k1 = 1; k1 < C; ++k1) a[k1] = cmul(a[k1], roots[k1 * G::M + n2]);
         if (i == 0) cluster_wait();   // every block of the cluster is running (the first time round)
 #pragma unroll
         for (int k1 = 0; k1 < C; ++k1) cluster.map_shared_rank(sm, k1)[PADDED ? smem_pos(n2, SC::PADSH) : n2] = a[k1];
@@ -122,7 +122,7 @@ cluster_fused_kernel(const float2* in, float2* out, int64_t ld, int valid, const
 #pragma unroll
         for (int r = 0; r < SC::R1; ++r) {
             const int n2 = lo + r * SC::S1;
-            v[s * SC::R1 + r] = cmulc(v[s * SC::R1 + r], roots[n2 * rank]);
+            v[s * SC::R1 + r] = cmulc(v[s * SC::R1 + r], roots[rank * G::M + n2]);
         }
     }
     cluster.sync();   // every block is done with its shared memory
@@ -163,7 +163,8 @@ cluster_fused_kernel(const float2* in, float2* out, int64_t ld, int valid, const
 // of shared memory), takes the inverse C-point DFTs and stores; a last
 // barrier keeps every block's shared memory until all pulls are done.
 template <class SC, int C, bool ROLL>
-__global__ void __launch_bounds__(SC::T, 65536 / (SC::T * 128) > 1 ? 65536 / (SC::T * 128) : 1)
+__global__ void __launch_bounds__(SC::T, SC::MINB > 0 ? SC::MINB
+                                                    : (65536 / (SC::T * 128) > 1 ? 65536 / (SC::T * 128) : 1))
 cluster_streamed_kernel(const float2* in, float2* out, int64_t ld, const float2* filt, const float2* tw) {
     namespace cg = cooperative_groups;
     using G = ClusterGeom<SC, C>;
@@ -211,7 +212,7 @@ cluster_streamed_kernel(const float2* in, float2* out, int64_t ld, const float2*
         grp_twiddle<R1, S1, true>(tw, lo, x);
         dft_reg<R1, true>(x);
 #pragma unroll
-        for (int r = 0; r < R1; ++r) x[r] = cmulc(x[r], roots[(lo + r * S1) * rank]);
+        for (int r = 0; r < R1; ++r) x[r] = cmulc(x[r], roots[rank * G::M + lo + r * S1]);
         grp_smem_store<R1, S1>(sm, lo, SC::PADSH, x);
     }
     cluster.sync();   // every block's inverse result is in place
@@ -371,13 +372,19 @@ constexpr SchedDesc make_cluster_desc(const char* name) {
 
 using M8192 = Sched<8192, 32, 16, 16, 32>;      // 256 threads, 66 KiB of shared memory per block
 using M16384 = Sched<16384, 32, 16, 32, 32>;    // 512 threads, 132 KiB
+using M4096 = Sched<4096, 32, 16, 16, 16>;      // 128 threads, 33 KiB, 4 blocks per SM (128 registers)
+using M4096b5 = Sched<4096, 32, 16, 16, 16, 5>; // the same, registers capped for 5 blocks per SM
+// first of each length: the fastest on GB300 (the autotuner times them all)
 const SchedDesc kTable[] = {
+    make_cluster_desc<M4096b5, 8, true>("n32768_c8_m4096_e32_sr_b5"),
+    make_cluster_desc<M4096, 8, true>("n32768_c8_m4096_e32_sr"),
+    make_cluster_desc<M8192, 8, true>("n65536_c8_m8192_e32_sr"),
+    make_cluster_desc<M8192, 16, true>("n131072_c16_m8192_e32_sr"),
+    make_cluster_desc<M4096, 16, true>("n65536_c16_m4096_e32_sr"),
     make_cluster_desc<M8192, 4, true>("n32768_c4_m8192_e32_sr"),
     make_cluster_desc<M16384, 2, true>("n32768_c2_m16384_e32_sr"),
-    make_cluster_desc<M8192, 8, true>("n65536_c8_m8192_e32_sr"),
     make_cluster_desc<M16384, 4, true>("n65536_c4_m16384_e32_sr"),
     make_cluster_desc<M16384, 8, true>("n131072_c8_m16384_e32_sr"),
-    make_cluster_desc<M8192, 16, true>("n131072_c16_m8192_e32_sr"),
     make_cluster_desc<M8192, 4>("n32768_c4_m8192_e32"),
     make_cluster_desc<M16384, 2>("n32768_c2_m16384_e32"),
     make_cluster_desc<M8192, 8>("n65536_c8_m8192_e32"),

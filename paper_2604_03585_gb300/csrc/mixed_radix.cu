@@ -10,8 +10,9 @@
 // R_i-point DFT in registers and (forward passes before the last) multiplies
 // element r by W_{R_i S_i}^{(g mod S_i) r}.  Positions never move, so after
 // the last pass position P = sum_i k_i S_i holds X[k_0 + R_0 (k_1 + R_1 (k_2
-// + ...))] (mixed-radix digit reversal); the filter is stored in exactly that
-// position order with 1/n folded in, and the inverse mirrors the passes with
+// + ...))] (mixed-radix digit reversal); the filter is stored in that order
+// with 1/n folded in (slot r (n / R_L) + q for position q R_L + r, so that
+// the last pass's lanes read it coalesced), and the inverse mirrors the passes with
 // conjugate twiddles back to natural order.  Twiddles and the filter order
 // are designed on the host and in FP64 at plan time.
 //
@@ -190,11 +191,16 @@ cudaError_t build_mixed_twiddles(int n, float2* tw, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// position P = sum_i k_i S_i -> frequency k_0 + R_0 (k_1 + R_1 (k_2 + ...))
+// The filter's slot order: slot j = r (n / R_L) + q holds position P =
+// q R_L + r (the last pass's group q, element r; consecutive groups, one per
+// lane, read consecutive slots), and position P = sum_i k_i S_i holds
+// frequency k_0 + R_0 (k_1 + R_1 (k_2 + ...)).
 void mixed_positions(int n, int32_t* idx) {
     MixedGeom g{};
     if (!geometry(n, g)) return;
-    for (int P = 0; P < n; ++P) {
+    const int RL = g.R[g.P - 1], ngl = n / RL;
+    for (int j = 0; j < n; ++j) {
+        const int P = (j % ngl) * RL + j / ngl;
         int rem = P, digits[kMaxPasses];
         for (int i = 0; i < g.P; ++i) {
             digits[i] = rem / g.S[i];
@@ -202,7 +208,7 @@ void mixed_positions(int n, int32_t* idx) {
         }
         int k = 0;
         for (int i = g.P - 1; i >= 0; --i) k = digits[i] + g.R[i] * k;
-        idx[P] = k;
+        idx[j] = k;
     }
 }
 

@@ -166,7 +166,7 @@ enum MMode { kFirst, kMid, kLast, kInvMid, kInvFirst };
 // global when P == 1); kInvMid smem -> conj twiddle -> IDFT -> smem; kInvFirst
 // smem -> conj twiddle -> IDFT -> global.
 template <int R, int MODE, bool SINGLE>
-__device__ __forceinline__ void mgroup(int g, int S, uint32_t M, const float2* src, float2* dst, float2* sm,
+__device__ __forceinline__ void mgroup(int g, int S, uint32_t M, int ng, const float2* src, float2* dst, float2* sm,
                                        const float2* twi, const float2* filt) {
     const int q = M ? (int)__umulhi((uint32_t)g, M) : g;   // M == 0: S == 1
     const int lo = g - q * S, base = q * R * S + lo;
@@ -182,7 +182,7 @@ __device__ __forceinline__ void mgroup(int g, int S, uint32_t M, const float2* s
         dft_any<R, false>(v);
         if constexpr (MODE == kLast) {
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[r] = cmul(v[r], filt[base + r]);
+            for (int r = 0; r < R; ++r) v[r] = cmul(v[r], filt[r * ng + g]);   // slot of position g R + r
             dft_any<R, true>(v);
         } else {
 #pragma unroll
@@ -205,7 +205,7 @@ __device__ __forceinline__ void mpass(int R, int S, uint32_t M, int n, int t, in
     const int ng = n / R;
 #define SAR_MIXED_CASE(RR)                                                                       \
     case RR:                                                                                     \
-        for (int g = t; g < ng; g += T) mgroup<RR, MODE, SINGLE>(g, S, M, src, dst, sm, twi, filt); \
+        for (int g = t; g < ng; g += T) mgroup<RR, MODE, SINGLE>(g, S, M, ng, src, dst, sm, twi, filt); \
         break;
     switch (R) {
         SAR_MIXED_CASE(2)

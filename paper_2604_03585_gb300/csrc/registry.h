@@ -49,9 +49,9 @@ struct SchedDesc {
     int cluster;            // > 1: one line per cluster of this many blocks, N = cluster * (n / cluster);
                             // e, r1..r3, rl, threads and smem_bytes then describe each block's
                             // M = n / cluster point engine, and the twiddle table is the M-point
-                            // engine's followed by W_N^j for j < n
+                            // engine's followed by W_N^{k1 n2} at k1 M + n2 (k1 < cluster, n2 < M)
     int mixed;              // 1: the mixed-radix engine of a 7-smooth length (mixed_radix.h): r1..r3
-                            // are its first radices, e is 0, the filter is in position order
+                            // are its first radices, e is 0, the filter is in the last pass's slot order
 };
 
 // All compiled schedules (one table per translation unit).

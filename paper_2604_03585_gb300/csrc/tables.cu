@@ -18,12 +18,17 @@ __global__ void twiddle_table_kernel(float2 *tw, int R, int S, int M) {
     tw[i] = make_float2((float)c, (float)s);
 }
 
-// out[j] = exp(-2 pi i j / n), j < n, evaluated like the twiddles above.
-__global__ void roots_table_kernel(float2 *out, int n) {
+// The four-step twiddles of a line of n = C m samples on a cluster of C
+// blocks: out[k1 m + n2] = exp(-2 pi i k1 n2 / n), k1 < C, n2 < m, evaluated
+// like the twiddles above (k1 n2 < n, no reduction needed).  Row k1 is the
+// twiddle set of one block of the cluster, contiguous in n2, so that a
+// warp's consecutive n2 read one run of the table.
+__global__ void roots_table_kernel(float2 *out, int n, int m) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
+    const long long e = (long long)(j / m) * (j % m);
     double s, c;
-    sincospi(-2.0 * (double)j / (double)n, &s, &c);
+    sincospi(-2.0 * (double)e / (double)n, &s, &c);
     out[j] = make_float2((float)c, (float)s);
 }
 
@@ -197,7 +202,7 @@ cudaError_t build_twiddles(const SchedDesc &d, float2 *tw, cudaStream_t st) {
         twiddle_table_kernel<<<(t2 + 255) / 256, 256, 0, st>>>(tw + total, d.r2, S2, S1);
         total += t2;
     }
-    if (d.cluster > 1) roots_table_kernel<<<(d.n + 255) / 256, 256, 0, st>>>(tw + total, d.n);
+    if (d.cluster > 1) roots_table_kernel<<<(d.n + 255) / 256, 256, 0, st>>>(tw + total, d.n, M);
     return cudaGetLastError();
 }
 

@@ -78,7 +78,9 @@ def test_lfm_spectrum_long(sar, orc, n):
 
 CLUSTER_SCHEDULES = [(n, f"n{n}_c{c}_m{m}_e32{v}") for (n, c, m) in
                      [(32768, 4, 8192), (32768, 2, 16384), (65536, 8, 8192), (65536, 4, 16384),
-                      (131072, 8, 16384), (131072, 16, 8192)] for v in ("", "_sr")]
+                      (131072, 8, 16384), (131072, 16, 8192)] for v in ("", "_sr")] + \
+                    [(n, f"n{n}_c{c}_m{m}_e32{v}") for (n, c, m, v) in
+                     [(32768, 8, 4096, "_sr"), (32768, 8, 4096, "_sr_b5"), (65536, 16, 4096, "_sr")]]
 
 
 def test_cluster_schedule_list_is_complete(sar):
