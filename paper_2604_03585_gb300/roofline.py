@@ -13,11 +13,11 @@ Pure host arithmetic; importing this module needs neither torch nor a GPU.
 """
 from __future__ import annotations
 
-import glob
 import hashlib
 import json
 import math
 import os
+import re
 
 C64 = 8  # bytes per complex64 sample
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -57,14 +57,27 @@ def rda_flops(n_az: int, n_range: int) -> float:
     return n_az * fused_line_flops(n_range) + n_range * fused_line_flops(n_az)
 
 
+def _local_includes(path: str, seen: set) -> None:
+    """`path` and every csrc file it includes with #include "...", recursively."""
+    if path in seen or not os.path.exists(path):
+        return
+    seen.add(path)
+    with open(path) as fh:
+        for line in fh:
+            m = re.match(r'\s*#\s*include\s+"([^"]+)"', line)
+            if m:
+                _local_includes(os.path.normpath(os.path.join(os.path.dirname(path), m.group(1))), seen)
+
+
 def kernel_source_hash() -> str:
-    """sha256 over the CUDA sources of the kernels whose traffic is recorded
-    (the line-engine headers, the 4096-point schedule table, the corner turn);
-    a recorded ncu traffic figure is valid only for this hash."""
+    """sha256 over the CUDA sources of the kernels whose traffic is recorded:
+    the 4096-point schedule table (the fused and folded range-pass kernels)
+    and every header it includes; a recorded ncu traffic figure is valid only
+    for this hash."""
     h = hashlib.sha256()
-    files = sorted(glob.glob(os.path.join(_HERE, "csrc", "*.cuh")) +
-                   glob.glob(os.path.join(_HERE, "csrc", "sched_4096.cu")) +
-                   glob.glob(os.path.join(_HERE, "csrc", "corner_turn.cu")))
+    seen: set = set()
+    _local_includes(os.path.join(_HERE, "csrc", "sched_4096.cu"), seen)
+    files = sorted(seen)
     for f in files:
         h.update(os.path.basename(f).encode())
         with open(f, "rb") as fh:
