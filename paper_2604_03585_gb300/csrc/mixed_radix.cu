@@ -31,6 +31,7 @@
 // instead of an integer division (exact for every index below 2^19).  The
 // kernel is compiled with registers capped for 2, 3 and 4 blocks per SM
 // (mixed_radix_k*.cu) and the variant is chosen by length.
+#include <cstdlib>
 #include <map>
 #include <mutex>
 #include <string>
@@ -136,6 +137,12 @@ cudaError_t launch_mixed(const float2* in, float2* out, int64_t n_lines, int64_t
     MixedGeom g{};
     if (!geometry(valid, g)) return cudaErrorInvalidValue;
     const int lpb = lines_per_block(g), smem = smem_bytes(g);
+    // SAR_MIXED_GENERIC=1: the runtime kernel even where a specialisation
+    // exists (the two give bit-identical results; tests compare them)
+    const char* generic = getenv("SAR_MIXED_GENERIC");
+    if (!(generic && generic[0] == '1'))
+        if (const mixed3_fn f = specialised(g, occupancy_variant(valid)))
+            return f(in, out, n_lines, ld, filt, tw, smem, st);
     switch (occupancy_variant(valid)) {
         case 4: return launch_k4(in, out, n_lines, ld, filt, tw, g, lpb, smem, st);
         case 3: return launch_k3(in, out, n_lines, ld, filt, tw, g, lpb, smem, st);
@@ -147,6 +154,7 @@ cudaError_t prepare_mixed() {
     cudaError_t e = set_smem_k2(kMixedSmemMax);
     if (e == cudaSuccess) e = set_smem_k3(kMixedSmemMax);
     if (e == cudaSuccess) e = set_smem_k4(kMixedSmemMax);
+    if (e == cudaSuccess) e = prepare_specialised();
     return e;
 }
 

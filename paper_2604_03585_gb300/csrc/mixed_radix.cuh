@@ -263,6 +263,47 @@ fused_mixed_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld, c
     if (live) mpass<kInvFirst, false>(geo.R[0], geo.S[0], geo.M[0], n, t, T, src, dst, sm, tw + geo.tw_off[0], filt);
 }
 
+// The same kernel for one three-pass length fixed at compile time (radices
+// RA, RB, RC, T threads per line): every stride, group split and table
+// offset becomes a constant, so the per-element index arithmetic of the
+// runtime kernel folds away.  Same passes, same arithmetic, same tables and
+// filter order; results are bit-identical to the runtime kernel's.
+__host__ __device__ constexpr uint32_t split_magic(int S) {
+    return S > 1 ? (uint32_t)((((uint64_t)1 << 32) + (uint64_t)S - 1) / (uint64_t)S) : 0u;
+}
+template <int N, int RA, int RB, int RC, int T, int MINB>
+__global__ void __launch_bounds__(kMixedThreads, MINB)
+fused_mixed3_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld, const float2* filt,
+                    const float2* tw) {
+    constexpr int SA = N / RA, SB = SA / RB;
+    static_assert(RA * RB * RC == N && SB == RC, "three radices of N");
+    static_assert(kMixedThreads % T == 0, "whole lines per block");
+    constexpr uint32_t MA = split_magic(SA), MB = split_magic(SB);
+    constexpr int LPB = kMixedThreads / T, PADN = N + (N >> 5) + 1;
+    extern __shared__ float2 smem_mixed[];
+    const int lib = threadIdx.x / T, t = threadIdx.x % T;
+    const int64_t line = (int64_t)blockIdx.x * LPB + lib;
+    const bool live = line < n_lines;
+    float2* sm = smem_mixed + lib * PADN;
+    const float2* src = in + (live ? line : 0) * ld;
+    float2* dst = out + (live ? line : 0) * ld;
+    const float2* twb = tw + RA * SA;   // the second pass's table
+    if (live)
+        for (int g = t; g < N / RA; g += T) mgroup<RA, kFirst, false>(g, SA, MA, N / RA, src, dst, sm, tw, filt);
+    __syncthreads();
+    if (live)
+        for (int g = t; g < N / RB; g += T) mgroup<RB, kMid, false>(g, SB, MB, N / RB, src, dst, sm, twb, filt);
+    __syncthreads();
+    if (live)
+        for (int g = t; g < N / RC; g += T) mgroup<RC, kLast, false>(g, 1, 0u, N / RC, src, dst, sm, tw, filt);
+    __syncthreads();
+    if (live)
+        for (int g = t; g < N / RB; g += T) mgroup<RB, kInvMid, false>(g, SB, MB, N / RB, src, dst, sm, twb, filt);
+    __syncthreads();
+    if (live)
+        for (int g = t; g < N / RA; g += T) mgroup<RA, kInvFirst, false>(g, SA, MA, N / RA, src, dst, sm, tw, filt);
+}
+
 // one occupancy variant of the kernel (mixed_radix_k<MINB>.cu)
 template <int MINB>
 cudaError_t launch_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld, const float2* filt,
@@ -285,6 +326,13 @@ SAR_MIXED_VARIANT_DECL(2)
 SAR_MIXED_VARIANT_DECL(3)
 SAR_MIXED_VARIANT_DECL(4)
 #undef SAR_MIXED_VARIANT_DECL
+
+// The compile-time specialisations (mixed_radix_ct.cu): the one of length n
+// whose radices and threads per line match g, or nullptr.
+typedef cudaError_t (*mixed3_fn)(const float2*, float2*, int64_t, int64_t, const float2*, const float2*, int,
+                                 cudaStream_t);
+mixed3_fn specialised(const MixedGeom& g, int minb);
+cudaError_t prepare_specialised();
 
 }  // namespace mixed
 }  // namespace sar

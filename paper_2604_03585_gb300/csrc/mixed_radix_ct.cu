@@ -1,0 +1,59 @@
+// Compile-time specialisations of the mixed-radix fused kernel for common
+// three-pass lengths (the runtime kernel serves every other length).  Each
+// entry repeats the host geometry of its length (radices, threads per line,
+// register cap); specialised() hands one out only when they agree.
+#include "mixed_radix.cuh"
+
+namespace sar {
+namespace mixed {
+
+namespace {
+
+template <int N, int RA, int RB, int RC, int T, int MINB>
+cudaError_t launch3(const float2* in, float2* out, int64_t n_lines, int64_t ld, const float2* filt, const float2* tw,
+                    int smem, cudaStream_t st) {
+    constexpr int LPB = kMixedThreads / T;
+    fused_mixed3_kernel<N, RA, RB, RC, T, MINB>
+        <<<(unsigned)((n_lines + LPB - 1) / LPB), kMixedThreads, smem, st>>>(in, out, n_lines, ld, filt, tw);
+    return cudaGetLastError();
+}
+template <int N, int RA, int RB, int RC, int T, int MINB>
+cudaError_t attr3() {
+    return cudaFuncSetAttribute(fused_mixed3_kernel<N, RA, RB, RC, T, MINB>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, kMixedSmemMax);
+}
+
+struct Spec {
+    int n, ra, rb, rc, t, minb;
+    mixed3_fn launch;
+    cudaError_t (*attr)();
+};
+#define SAR_SPEC(N, RA, RB, RC, T, MB) \
+    Spec{N, RA, RB, RC, T, MB, &launch3<N, RA, RB, RC, T, MB>, &attr3<N, RA, RB, RC, T, MB>}
+const Spec kSpecs[] = {
+    SAR_SPEC(1000, 10, 10, 10, 64, 4),  SAR_SPEC(2000, 20, 10, 10, 128, 4), SAR_SPEC(3000, 20, 15, 10, 256, 4),
+    SAR_SPEC(4000, 20, 20, 10, 256, 4), SAR_SPEC(5000, 25, 20, 10, 256, 3), SAR_SPEC(6000, 20, 20, 15, 256, 3),
+    SAR_SPEC(8000, 20, 20, 20, 256, 2),
+};
+#undef SAR_SPEC
+
+}  // namespace
+
+mixed3_fn specialised(const MixedGeom& g, int minb) {
+    if (g.P != 3) return nullptr;
+    for (const Spec& s : kSpecs)
+        if (s.n == g.n && s.ra == g.R[0] && s.rb == g.R[1] && s.rc == g.R[2] && s.t == g.T && s.minb == minb)
+            return s.launch;
+    return nullptr;
+}
+
+cudaError_t prepare_specialised() {
+    for (const Spec& s : kSpecs) {
+        const cudaError_t e = s.attr();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace mixed
+}  // namespace sar
