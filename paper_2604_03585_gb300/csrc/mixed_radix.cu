@@ -141,7 +141,7 @@ cudaError_t launch_mixed(const float2* in, float2* out, int64_t n_lines, int64_t
     // exists (the two give bit-identical results; tests compare them)
     const char* generic = getenv("SAR_MIXED_GENERIC");
     if (!(generic && generic[0] == '1'))
-        if (const mixed3_fn f = specialised(g, occupancy_variant(valid)))
+        if (const mixed3_fn f = specialised(g))
             return f(in, out, n_lines, ld, filt, tw, smem, st);
     switch (occupancy_variant(valid)) {
         case 4: return launch_k4(in, out, n_lines, ld, filt, tw, g, lpb, smem, st);

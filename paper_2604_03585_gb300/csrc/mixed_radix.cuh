@@ -331,7 +331,7 @@ SAR_MIXED_VARIANT_DECL(4)
 // whose radices and threads per line match g, or nullptr.
 typedef cudaError_t (*mixed3_fn)(const float2*, float2*, int64_t, int64_t, const float2*, const float2*, int,
                                  cudaStream_t);
-mixed3_fn specialised(const MixedGeom& g, int minb);
+mixed3_fn specialised(const MixedGeom& g);
 cudaError_t prepare_specialised();
 
 }  // namespace mixed

@@ -1,7 +1,8 @@
 // Compile-time specialisations of the mixed-radix fused kernel for common
 // three-pass lengths (the runtime kernel serves every other length).  Each
-// entry repeats the host geometry of its length (radices, threads per line,
-// register cap); specialised() hands one out only when they agree.
+// entry repeats the host geometry of its length (radices, threads per line);
+// specialised() hands one out only when they agree.  The register cap (blocks
+// per SM) of each is the fastest of 2 ... 5 in a sweep on GB300.
 #include "mixed_radix.cuh"
 
 namespace sar {
@@ -32,18 +33,17 @@ struct Spec {
     Spec{N, RA, RB, RC, T, MB, &launch3<N, RA, RB, RC, T, MB>, &attr3<N, RA, RB, RC, T, MB>}
 const Spec kSpecs[] = {
     SAR_SPEC(1000, 10, 10, 10, 64, 4),  SAR_SPEC(2000, 20, 10, 10, 128, 4), SAR_SPEC(3000, 20, 15, 10, 256, 4),
-    SAR_SPEC(4000, 20, 20, 10, 256, 4), SAR_SPEC(5000, 25, 20, 10, 256, 3), SAR_SPEC(6000, 20, 20, 15, 256, 3),
+    SAR_SPEC(4000, 20, 20, 10, 256, 3), SAR_SPEC(5000, 25, 20, 10, 256, 3), SAR_SPEC(6000, 20, 20, 15, 256, 3),
     SAR_SPEC(8000, 20, 20, 20, 256, 2),
 };
 #undef SAR_SPEC
 
 }  // namespace
 
-mixed3_fn specialised(const MixedGeom& g, int minb) {
+mixed3_fn specialised(const MixedGeom& g) {
     if (g.P != 3) return nullptr;
     for (const Spec& s : kSpecs)
-        if (s.n == g.n && s.ra == g.R[0] && s.rb == g.R[1] && s.rc == g.R[2] && s.t == g.T && s.minb == minb)
-            return s.launch;
+        if (s.n == g.n && s.ra == g.R[0] && s.rb == g.R[1] && s.rc == g.R[2] && s.t == g.T) return s.launch;
     return nullptr;
 }
 
