@@ -165,7 +165,17 @@ enum MMode { kFirst, kMid, kLast, kInvMid, kInvFirst };
 // -> smem; kLast (src global when P == 1) -> DFT -> filter -> IDFT -> smem (or
 // global when P == 1); kInvMid smem -> conj twiddle -> IDFT -> smem; kInvFirst
 // smem -> conj twiddle -> IDFT -> global.
-template <int R, int MODE, bool SINGLE>
+// shared-memory slot of position p: one pad slot per 32 positions, or with
+// PADDIV > 0 one per PADDIV positions
+template <int PADDIV>
+__device__ __forceinline__ int mslot(int p) {
+    if constexpr (PADDIV > 0)
+        return p + p / PADDIV;
+    else
+        return mpad(p);
+}
+
+template <int R, int MODE, bool SINGLE, int PADDIV = 0>
 __device__ __forceinline__ void mgroup(int g, int S, uint32_t M, int ng, const float2* src, float2* dst, float2* sm,
                                        const float2* twi, const float2* filt) {
     const int q = M ? (int)__umulhi((uint32_t)g, M) : g;   // M == 0: S == 1
@@ -173,7 +183,7 @@ __device__ __forceinline__ void mgroup(int g, int S, uint32_t M, int ng, const f
     float2 v[R];
     const bool from_global = MODE == kFirst || (MODE == kLast && SINGLE);
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = from_global ? __ldcs(src + base + r * S) : sm[mpad(base + r * S)];
+    for (int r = 0; r < R; ++r) v[r] = from_global ? __ldcs(src + base + r * S) : sm[mslot<PADDIV>(base + r * S)];
     if constexpr (MODE == kInvMid || MODE == kInvFirst) {
 #pragma unroll
         for (int r = 1; r < R; ++r) v[r] = cmulc(v[r], twi[r * S + lo]);
@@ -195,7 +205,7 @@ __device__ __forceinline__ void mgroup(int g, int S, uint32_t M, int ng, const f
         if (to_global)
             __stcs(dst + base + r * S, v[r]);
         else
-            sm[mpad(base + r * S)] = v[r];
+            sm[mslot<PADDIV>(base + r * S)] = v[r];
     }
 }
 
@@ -271,7 +281,14 @@ fused_mixed_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld, c
 __host__ __device__ constexpr uint32_t split_magic(int S) {
     return S > 1 ? (uint32_t)((((uint64_t)1 << 32) + (uint64_t)S - 1) / (uint64_t)S) : 0u;
 }
-template <int N, int RA, int RB, int RC, int T, int MINB>
+// PADDIV: the shared-memory padding (0: one slot per 32 positions, as the
+// runtime kernel; else one per PADDIV, chosen per length from a simulation
+// of every pass's bank pairs); mixed3_smem is the block's shared memory.
+template <int N, int T, int PADDIV>
+__host__ __device__ constexpr int mixed3_smem() {
+    return (kMixedThreads / T) * (N + (PADDIV > 0 ? N / PADDIV : N >> 5) + 1) * (int)sizeof(float2);
+}
+template <int N, int RA, int RB, int RC, int T, int MINB, int PADDIV>
 __global__ void __launch_bounds__(kMixedThreads, MINB)
 fused_mixed3_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld, const float2* filt,
                     const float2* tw) {
@@ -279,7 +296,7 @@ fused_mixed3_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld, 
     static_assert(RA * RB * RC == N && SB == RC, "three radices of N");
     static_assert(kMixedThreads % T == 0, "whole lines per block");
     constexpr uint32_t MA = split_magic(SA), MB = split_magic(SB);
-    constexpr int LPB = kMixedThreads / T, PADN = N + (N >> 5) + 1;
+    constexpr int LPB = kMixedThreads / T, PADN = mixed3_smem<N, T, PADDIV>() / LPB / (int)sizeof(float2);
     extern __shared__ float2 smem_mixed[];
     const int lib = threadIdx.x / T, t = threadIdx.x % T;
     const int64_t line = (int64_t)blockIdx.x * LPB + lib;
@@ -289,19 +306,19 @@ fused_mixed3_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld, 
     float2* dst = out + (live ? line : 0) * ld;
     const float2* twb = tw + RA * SA;   // the second pass's table
     if (live)
-        for (int g = t; g < N / RA; g += T) mgroup<RA, kFirst, false>(g, SA, MA, N / RA, src, dst, sm, tw, filt);
+        for (int g = t; g < N / RA; g += T) mgroup<RA, kFirst, false, PADDIV>(g, SA, MA, N / RA, src, dst, sm, tw, filt);
     __syncthreads();
     if (live)
-        for (int g = t; g < N / RB; g += T) mgroup<RB, kMid, false>(g, SB, MB, N / RB, src, dst, sm, twb, filt);
+        for (int g = t; g < N / RB; g += T) mgroup<RB, kMid, false, PADDIV>(g, SB, MB, N / RB, src, dst, sm, twb, filt);
     __syncthreads();
     if (live)
-        for (int g = t; g < N / RC; g += T) mgroup<RC, kLast, false>(g, 1, 0u, N / RC, src, dst, sm, tw, filt);
+        for (int g = t; g < N / RC; g += T) mgroup<RC, kLast, false, PADDIV>(g, 1, 0u, N / RC, src, dst, sm, tw, filt);
     __syncthreads();
     if (live)
-        for (int g = t; g < N / RB; g += T) mgroup<RB, kInvMid, false>(g, SB, MB, N / RB, src, dst, sm, twb, filt);
+        for (int g = t; g < N / RB; g += T) mgroup<RB, kInvMid, false, PADDIV>(g, SB, MB, N / RB, src, dst, sm, twb, filt);
     __syncthreads();
     if (live)
-        for (int g = t; g < N / RA; g += T) mgroup<RA, kInvFirst, false>(g, SA, MA, N / RA, src, dst, sm, tw, filt);
+        for (int g = t; g < N / RA; g += T) mgroup<RA, kInvFirst, false, PADDIV>(g, SA, MA, N / RA, src, dst, sm, tw, filt);
 }
 
 // one occupancy variant of the kernel (mixed_radix_k<MINB>.cu)
