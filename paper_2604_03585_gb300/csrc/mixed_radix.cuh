@@ -306,19 +306,24 @@ fused_mixed3_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld, 
     float2* dst = out + (live ? line : 0) * ld;
     const float2* twb = tw + RA * SA;   // the second pass's table
     if (live)
-        for (int g = t; g < N / RA; g += T) mgroup<RA, kFirst, false, PADDIV>(g, SA, MA, N / RA, src, dst, sm, tw, filt);
+        for (int g = t; g < N / RA; g += T)
+            mgroup<RA, kFirst, false, PADDIV>(g, SA, MA, N / RA, src, dst, sm, tw, filt);
     __syncthreads();
     if (live)
-        for (int g = t; g < N / RB; g += T) mgroup<RB, kMid, false, PADDIV>(g, SB, MB, N / RB, src, dst, sm, twb, filt);
+        for (int g = t; g < N / RB; g += T)
+            mgroup<RB, kMid, false, PADDIV>(g, SB, MB, N / RB, src, dst, sm, twb, filt);
     __syncthreads();
     if (live)
-        for (int g = t; g < N / RC; g += T) mgroup<RC, kLast, false, PADDIV>(g, 1, 0u, N / RC, src, dst, sm, tw, filt);
+        for (int g = t; g < N / RC; g += T)
+            mgroup<RC, kLast, false, PADDIV>(g, 1, 0u, N / RC, src, dst, sm, tw, filt);
     __syncthreads();
     if (live)
-        for (int g = t; g < N / RB; g += T) mgroup<RB, kInvMid, false, PADDIV>(g, SB, MB, N / RB, src, dst, sm, twb, filt);
+        for (int g = t; g < N / RB; g += T)
+            mgroup<RB, kInvMid, false, PADDIV>(g, SB, MB, N / RB, src, dst, sm, twb, filt);
     __syncthreads();
     if (live)
-        for (int g = t; g < N / RA; g += T) mgroup<RA, kInvFirst, false, PADDIV>(g, SA, MA, N / RA, src, dst, sm, tw, filt);
+        for (int g = t; g < N / RA; g += T)
+            mgroup<RA, kInvFirst, false, PADDIV>(g, SA, MA, N / RA, src, dst, sm, tw, filt);
 }
 
 // one occupancy variant of the kernel (mixed_radix_k<MINB>.cu)
