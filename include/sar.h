@@ -122,7 +122,8 @@ typedef struct {
  *     length L >= 2n - 1 (filter FFT_L(IFFT_n(H)) designed in FP64 at plan
  *     time);
  * one fused launch per pass either way, as for powers of two.  The unfused
- * pipeline and split precision need powers of two.  Allocates the
+ * pipeline needs a transform at the length itself (powers of two and the
+ * mixed-radix lengths); split precision needs powers of two.  Allocates the
  * plan's device tables on the current device, builds them (FP64 twiddle
  * phases rounded to FP32) and synchronises the device once; not for the hot
  * loop.  *out receives the plan, or NULL on failure. */
@@ -285,12 +286,15 @@ SAR_API sar_status sar_simulate_echo(int64_t n_az, int64_t n_range, const int64_
  * out[l][k] = sum_j in[l][j] exp(-+2 pi i j k / n), '+' when inverse != 0
  * (computed as conj(FFT(conj x)), Sec. II-C).  in and out: device
  * complex64[n_lines][n]; in place allowed.  n: power of two in [256, 131072],
- * or any other length in [2, 8192]: then the DFT by Bluestein's identity
- * jk = (j^2 + k^2 - (k-j)^2)/2, a chirp multiply (c_m = exp(-i pi m^2 / n),
- * phases reduced exactly mod 2n in FP64), a linear convolution with conj(c)
- * through the power-of-two engine at L >= 2n - 1 (filter designed in FP64 on
- * the first call per length and cached, which allocates) and a chirp multiply
- * of the output, in one kernel.
+ * or any other length in [2, 8192]: a length of the mixed-radix engine (prime
+ * factors 2, 3, 5, 7; see sar_plan_create) runs its forward passes at n and
+ * writes the spectrum in natural order; any other length takes the DFT by
+ * Bluestein's identity jk = (j^2 + k^2 - (k-j)^2)/2, a chirp multiply
+ * (c_m = exp(-i pi m^2 / n), phases reduced exactly mod 2n in FP64), a linear
+ * convolution with conj(c) through the power-of-two engine at L >= 2n - 1
+ * (filter designed in FP64 on the first call per length and cached, which
+ * allocates) and a chirp multiply of the output, in one kernel.  Either way
+ * the first call per length builds and caches its tables (allocates).
  * Exposes the line FFT engine on its own (tests, filter design). */
 SAR_API sar_status sar_fft_lines(int64_t n, int64_t n_lines, const void *in, void *out, int inverse, sar_stream stream);
 

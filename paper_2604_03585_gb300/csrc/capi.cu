@@ -766,7 +766,8 @@ sar_status sar_rda_process_oop(sar_plan p, const void *raw, void *work, void *im
 // line instead of two).
 static bool unfused_ok(const LinePlan &lp) { return lp.n == lp.sched->n && lp.sched->dft; }
 static sar_status unfused_refusal() {
-    return fail(SAR_ERR_UNSUPPORTED, "the unfused pipeline needs power-of-two line lengths");
+    return fail(SAR_ERR_UNSUPPORTED,
+                "the unfused pipeline needs line lengths with their own engine (powers of two, prime factors 2, 3, 5, 7)");
 }
 
 static sar_status run_unfused(const sar_plan_s *p, const LinePlan &lp, int64_t n_lines, void *data, cudaStream_t s) {
@@ -1052,8 +1053,24 @@ sar_status sar_rda_process_host_n(sar_plan p, int32_t n_scenes, const void *cons
 
 sar_status sar_fft_lines(int64_t n, int64_t n_lines, const void *in, void *out, int inverse, sar_stream stream) {
     sar_status st;
+    if (!native_length(n) && sar::mixed_length((int)n)) {
+        // prime factors 2, 3, 5, 7 only: the mixed-radix engine at n itself
+        if (n_lines < 0) return fail(SAR_ERR_INVALID_ARG, "n_lines < 0");
+        if (n_lines == 0) return SAR_OK;
+        if ((st = check_device_ptr(in, "in")) != SAR_OK) return st;
+        if ((st = check_device_ptr(out, "out")) != SAR_OK) return st;
+        if (in != out && overlaps(in, out, sizeof(float2) * (size_t)(n * n_lines)))
+            return fail(SAR_ERR_INVALID_ARG, "in and out partially overlap");
+        const SchedDesc *d = sar::mixed_schedule((int)n);
+        float2 *tw = nullptr;
+        if ((st = cached_twiddles(d, &tw)) != SAR_OK) return st;
+        cudaError_t e = d->dft((const float2 *)in, (float2 *)out, n_lines, n, (int)n, tw, inverse ? 1 : 0,
+                               (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "fft launch");
+        return SAR_OK;
+    }
     if (!native_length(n) && n >= 2 && n <= 8192) {
-        // a length that is not a power of two: Bluestein on the length-L engine
+        // any other length that is not a power of two: Bluestein on the length-L engine
         if (n_lines < 0) return fail(SAR_ERR_INVALID_ARG, "n_lines < 0");
         if (n_lines == 0) return SAR_OK;
         if ((st = check_device_ptr(in, "in")) != SAR_OK) return st;

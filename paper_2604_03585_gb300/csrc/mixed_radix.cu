@@ -47,6 +47,19 @@ namespace sar {
 namespace mixed {
 // tw[off_i + r S_i + lo] = exp(-2 pi i lo r / (R_i S_i)), FP64 phases rounded
 // once (the exponent lo r reduced modulo R_i S_i exactly, in integers)
+// pos[k] = sum_i k_i S_i for k = k_0 + R_0 (k_1 + R_1 (k_2 + ...)): where the
+// forward passes leave frequency k
+__global__ void mixed_positions_kernel(int32_t* pos, MixedGeom g) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.n) return;
+    int rem = k, p = 0;
+    for (int i = 0; i < g.P; ++i) {
+        p += (rem % g.R[i]) * g.S[i];
+        rem /= g.R[i];
+    }
+    pos[k] = p;
+}
+
 __global__ void mixed_twiddle_kernel(float2* tw, int R, int S) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= R * S) return;
@@ -108,6 +121,7 @@ bool geometry(int n, MixedGeom& g) {
         if (i < g.P - 1) off += g.R[i] * g.S[i];
         if (i < g.P && n / g.R[i] > most) most = n / g.R[i];
     }
+    g.pos_off = off;
     // threads per line: a power of two covering about half the largest group
     // count of a pass (one or two groups per thread), 32 ... kMixedThreads
     g.T = 32;
@@ -117,11 +131,8 @@ bool geometry(int n, MixedGeom& g) {
     return true;
 }
 
-int twiddle_elems(const MixedGeom& g) {
-    int e = 0;
-    for (int i = 0; i < g.P - 1; ++i) e += g.R[i] * g.S[i];
-    return e > 0 ? e : 1;
-}
+// the inter-pass twiddles, then the plain transform's position table
+int twiddle_elems(const MixedGeom& g) { return g.pos_off + (g.n + 1) / 2; }
 
 int lines_per_block(const MixedGeom& g) { return kMixedThreads / g.T; }
 int smem_bytes(const MixedGeom& g) { return lines_per_block(g) * (g.n + (g.n >> 5) + 1) * (int)sizeof(float2); }
@@ -150,11 +161,23 @@ cudaError_t launch_mixed(const float2* in, float2* out, int64_t n_lines, int64_t
     }
 }
 
+cudaError_t launch_mixed_dft(const float2* in, float2* out, int64_t n_lines, int64_t ld, int valid, const float2* tw,
+                             int inverse, cudaStream_t st) {
+    if (n_lines <= 0) return cudaSuccess;
+    MixedGeom g{};   // whole lines: valid is the length (as in launch_mixed)
+    if (!geometry(valid, g)) return cudaErrorInvalidValue;
+    const char* generic = getenv("SAR_MIXED_GENERIC");
+    if (!(generic && generic[0] == '1'))
+        if (const mixed3_dft_fn f = specialised_dft(g)) return f(in, out, n_lines, ld, valid, tw, g.pos_off, inverse, st);
+    return launch_dft_mixed(in, out, n_lines, ld, valid, tw, inverse, g, lines_per_block(g), smem_bytes(g), st);
+}
+
 cudaError_t prepare_mixed() {
     cudaError_t e = set_smem_k2(kMixedSmemMax);
     if (e == cudaSuccess) e = set_smem_k3(kMixedSmemMax);
     if (e == cudaSuccess) e = set_smem_k4(kMixedSmemMax);
     if (e == cudaSuccess) e = prepare_specialised();
+    if (e == cudaSuccess) e = set_smem_dft(kMixedSmemMax);
     return e;
 }
 
@@ -183,7 +206,7 @@ const SchedDesc* mixed_schedule(int n) {
     for (int i = 0; i < g.P; ++i) e->name += (i ? "x" : "") + std::to_string(g.R[i]);
     e->desc = SchedDesc{e->name.c_str(), n, 0, g.R[0], g.P > 1 ? g.R[1] : 1, g.P > 2 ? g.R[2] : 1,
                         lines_per_block(g), kMixedThreads, smem_bytes(g), twiddle_elems(g), g.R[g.P - 1], 0,
-                        &launch_mixed, nullptr, &prepare_mixed, nullptr, 0, nullptr, 0};
+                        &launch_mixed, &launch_mixed_dft, &prepare_mixed, nullptr, 0, nullptr, 0};
     e->desc.mixed = 1;
     g_descs[n] = e;
     return &e->desc;
@@ -196,6 +219,7 @@ cudaError_t build_mixed_twiddles(int n, float2* tw, cudaStream_t st) {
         const int cnt = g.R[i] * g.S[i];
         mixed_twiddle_kernel<<<(cnt + 255) / 256, 256, 0, st>>>(tw + g.tw_off[i], g.R[i], g.S[i]);
     }
+    mixed_positions_kernel<<<(n + 255) / 256, 256, 0, st>>>(reinterpret_cast<int32_t*>(tw + g.pos_off), g);
     return cudaGetLastError();
 }
 

@@ -21,6 +21,8 @@ struct MixedGeom {
     uint32_t M[kMaxPasses];   // ceil(2^32 / S): g / S == umulhi(g, M) for every g < 8192 and 2 <= S <= 8192
                               // (checked exhaustively); 0 for S == 1
     int T;                    // threads per line; kMixedThreads / T lines per block
+    int pos_off;              // float2 offset in the table of pos[k] (int32, k < n): the position that
+                              // holds frequency k after the forward passes (the plain transform's order)
 };
 
 __device__ __forceinline__ int mpad(int p) { return p + (p >> 5); }
@@ -159,12 +161,8 @@ __device__ __forceinline__ void dft_any(float2 (&v)[R]) {
 }
 
 // ---- one group of one pass ---------------------------------------------------
-enum MMode { kFirst, kMid, kLast, kInvMid, kInvFirst };
+enum MMode { kFirst, kMid, kLast, kInvMid, kInvFirst, kLastDft };
 
-// MODE: kFirst global -> DFT -> twiddle -> smem; kMid smem -> DFT -> twiddle
-// -> smem; kLast (src global when P == 1) -> DFT -> filter -> IDFT -> smem (or
-// global when P == 1); kInvMid smem -> conj twiddle -> IDFT -> smem; kInvFirst
-// smem -> conj twiddle -> IDFT -> global.
 // shared-memory slot of position p: one pad slot per 32 positions, or with
 // PADDIV > 0 one per PADDIV positions
 template <int PADDIV>
@@ -175,6 +173,11 @@ __device__ __forceinline__ int mslot(int p) {
         return mpad(p);
 }
 
+// MODE: kFirst global -> DFT -> twiddle -> smem; kMid smem -> DFT -> twiddle
+// -> smem; kLast (src global when P == 1) -> DFT -> filter -> IDFT -> smem (or
+// global when P == 1); kInvMid smem -> conj twiddle -> IDFT -> smem; kInvFirst
+// smem -> conj twiddle -> IDFT -> global; kLastDft smem -> DFT -> smem (the
+// last pass of a plain transform).
 template <int R, int MODE, bool SINGLE, int PADDIV = 0>
 __device__ __forceinline__ void mgroup(int g, int S, uint32_t M, int ng, const float2* src, float2* dst, float2* sm,
                                        const float2* twi, const float2* filt) {
@@ -194,6 +197,8 @@ __device__ __forceinline__ void mgroup(int g, int S, uint32_t M, int ng, const f
 #pragma unroll
             for (int r = 0; r < R; ++r) v[r] = cmul(v[r], filt[r * ng + g]);   // slot of position g R + r
             dft_any<R, true>(v);
+        } else if constexpr (MODE == kLastDft) {
+            // the spectrum stays in position order
         } else {
 #pragma unroll
             for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twi[r * S + lo]);
@@ -326,6 +331,51 @@ fused_mixed3_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld, 
             mgroup<RA, kInvFirst, false, PADDIV>(g, SA, MA, N / RA, src, dst, sm, tw, filt);
 }
 
+// The plain transform of the same compile-time length (the forward passes,
+// then natural order through the position table after the twiddles; sgn =
+// -1 conjugates input and output for the inverse).
+template <int N, int RA, int RB, int RC, int T, int MINB, int PADDIV>
+__global__ void __launch_bounds__(kMixedThreads, MINB)
+mixed3_dft_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld, int valid, const float2* tw,
+                  int pos_off, float sgn) {
+    constexpr int SA = N / RA, SB = SA / RB;
+    static_assert(RA * RB * RC == N && SB == RC, "three radices of N");
+    constexpr uint32_t MA = split_magic(SA), MB = split_magic(SB);
+    constexpr int LPB = kMixedThreads / T, PADN = mixed3_smem<N, T, PADDIV>() / LPB / (int)sizeof(float2);
+    extern __shared__ float2 smem_mixed[];
+    const int lib = threadIdx.x / T, t = threadIdx.x % T;
+    const int64_t line = (int64_t)blockIdx.x * LPB + lib;
+    const bool live = line < n_lines;
+    float2* sm = smem_mixed + lib * PADN;
+    const float2* src = in + (live ? line : 0) * ld;
+    float2* dst = out + (live ? line : 0) * ld;
+    const float2* twb = tw + RA * SA;
+    if (live)
+        for (int p = t; p < N; p += T) {
+            const float2 x = p < valid ? __ldcs(src + p) : make_float2(0.f, 0.f);
+            sm[mslot<PADDIV>(p)] = make_float2(x.x, sgn * x.y);
+        }
+    __syncthreads();
+    if (live)
+        for (int g = t; g < N / RA; g += T)
+            mgroup<RA, kMid, false, PADDIV>(g, SA, MA, N / RA, src, dst, sm, tw, tw);
+    __syncthreads();
+    if (live)
+        for (int g = t; g < N / RB; g += T)
+            mgroup<RB, kMid, false, PADDIV>(g, SB, MB, N / RB, src, dst, sm, twb, tw);
+    __syncthreads();
+    if (live)
+        for (int g = t; g < N / RC; g += T)
+            mgroup<RC, kLastDft, false, PADDIV>(g, 1, 0u, N / RC, src, dst, sm, tw, tw);
+    __syncthreads();
+    const int32_t* pos = reinterpret_cast<const int32_t*>(tw + pos_off);
+    if (live)
+        for (int k = t; k < N; k += T) {
+            const float2 x = sm[mslot<PADDIV>(pos[k])];
+            __stcs(dst + k, make_float2(x.x, sgn * x.y));
+        }
+}
+
 // one occupancy variant of the kernel (mixed_radix_k<MINB>.cu)
 template <int MINB>
 cudaError_t launch_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld, const float2* filt,
@@ -349,11 +399,20 @@ SAR_MIXED_VARIANT_DECL(3)
 SAR_MIXED_VARIANT_DECL(4)
 #undef SAR_MIXED_VARIANT_DECL
 
+// The plain transform (mixed_radix_dft.cu): the forward passes, then natural
+// order; the inverse as conj(DFT(conj x)), unnormalised.
+cudaError_t launch_dft_mixed(const float2* in, float2* out, int64_t n_lines, int64_t ld, int valid, const float2* tw,
+                             int inverse, const MixedGeom& g, int lines_per_block, int smem, cudaStream_t st);
+cudaError_t set_smem_dft(int bytes);
+
 // The compile-time specialisations (mixed_radix_ct.cu): the one of length n
 // whose radices and threads per line match g, or nullptr.
 typedef cudaError_t (*mixed3_fn)(const float2*, float2*, int64_t, int64_t, const float2*, const float2*, int,
                                  cudaStream_t);
+typedef cudaError_t (*mixed3_dft_fn)(const float2*, float2*, int64_t, int64_t, int, const float2*, int, int,
+                                     cudaStream_t);
 mixed3_fn specialised(const MixedGeom& g);
+mixed3_dft_fn specialised_dft(const MixedGeom& g);
 cudaError_t prepare_specialised();
 
 }  // namespace mixed

@@ -95,19 +95,24 @@ def test_line_compression_any_length(sar, orc, n, lines):
 @pytest.mark.parametrize("n,lines", [(1000, 13), (2000, 7), (3000, 5), (4000, 5), (5000, 3), (6000, 3),
                                      (8000, 3)])
 def test_specialised_mixed_kernel_equals_runtime_kernel(sar, n, lines, monkeypatch):
-    """The kernel compiled for one length and the runtime-radix kernel run the
-    same passes on the same tables: bit-identical results."""
+    """The kernels compiled for one length and the runtime-radix kernels run
+    the same passes on the same tables: bit-identical results, for the fused
+    compression and for the plain transform both ways."""
     x = dev(noise(41 + n, lines, n))
     Hr = dev(noise(8, 1, n)[0])
     plan = sar.sar_plan_create(n, lines, Hr, dev(np.ones(lines)))
-    a, b = torch.empty_like(x), torch.empty_like(x)
-    sar.sar_range_compress_oop(plan, x, a)
-    torch.cuda.synchronize()
-    monkeypatch.setenv("SAR_MIXED_GENERIC", "1")
-    sar.sar_range_compress_oop(plan, x, b)
-    torch.cuda.synchronize()
+    outs = []
+    for generic in ("0", "1"):
+        monkeypatch.setenv("SAR_MIXED_GENERIC", generic)
+        c, f, i = torch.empty_like(x), torch.empty_like(x), torch.empty_like(x)
+        sar.sar_range_compress_oop(plan, x, c)
+        sar.sar_fft_lines(n, lines, x, f, False)
+        sar.sar_fft_lines(n, lines, x, i, True)
+        torch.cuda.synchronize()
+        outs.append((c, f, i))
     plan.destroy()
-    assert torch.equal(a, b)
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
 
 
 @pytest.mark.parametrize("n_az,n_range", [(300, 1000), (256, 3000), (1000, 256), (300, 4096), (33, 77)])
@@ -168,9 +173,12 @@ def test_any_length_refusals(sar):
     with pytest.raises(sar.SarError) as e:
         sar.sar_plan_create_ex(1000, 256, a, b, range_schedule="n1024_e32_r32x32_l4")
     assert e.value.status == sar.SAR_ERR_INVALID_ARG
-    plan = sar.sar_plan_create(1000, 256, a, b)
-    x = torch.zeros((256, 1000), dtype=torch.complex64, device="cuda")
-    img = torch.empty((1000, 256), dtype=torch.complex64, device="cuda")
+    # the unfused pipeline needs a transform at the line length itself: the
+    # zero-padded convolution of 1009 has none
+    a9 = dev(np.ones(1009))
+    plan = sar.sar_plan_create(1009, 256, a9, b)
+    x = torch.zeros((256, 1009), dtype=torch.complex64, device="cuda")
+    img = torch.empty((1009, 256), dtype=torch.complex64, device="cuda")
     for call in (lambda: sar.sar_range_compress_unfused(plan, x),
                  lambda: sar.sar_rda_process_unfused(plan, x, img)):
         with pytest.raises(sar.SarError) as e:
@@ -180,6 +188,8 @@ def test_any_length_refusals(sar):
     torch.cuda.synchronize()
     assert float(img.abs().max()) == 0.0
     plan.destroy()
+    x = torch.zeros((256, 1000), dtype=torch.complex64, device="cuda")
+    img = torch.empty((1000, 256), dtype=torch.complex64, device="cuda")
     plan = sar.sar_plan_create(256, 1000, b, a)
     sar.sar_plan_set_geometry(plan, 10.0, 0.3, 100.0, 16)
     with pytest.raises(sar.SarError) as e:
@@ -188,8 +198,29 @@ def test_any_length_refusals(sar):
     plan.destroy()
 
 
+@pytest.mark.parametrize("n_az,n_range", [(256, 1000), (300, 3000)])
+def test_unfused_pipeline_at_seven_smooth_lengths(sar, orc, n_az, n_range):
+    """The unfused comparison pipeline (DFT kernel, spectrum multiply, inverse
+    DFT kernel) at a 7-smooth range length runs on the mixed-radix engine's
+    plain transform: the same image as the fused path, to rounding."""
+    x = noise(61 + n_range, n_az, n_range)
+    Hr = orc.matched_filter(n_range, sarsim.lfm_chirp(n_range // 8, n_range / 16.0))
+    Ha = orc.matched_filter(n_az, sarsim.lfm_chirp(64, 16.0))
+    plan = sar.sar_plan_create(n_range, n_az, dev(Hr), dev(Ha))
+    a = dev(x)
+    b = dev(x)
+    sar.sar_range_compress(plan, a)
+    sar.sar_range_compress_unfused(plan, b)
+    torch.cuda.synchronize()
+    ref = orc.compress_lines(x, Hr, nthreads=NTHREADS)
+    assert M.rel_l2(a.cpu().numpy(), ref) < LINE_TOL
+    assert M.rel_l2(b.cpu().numpy(), ref) < LINE_TOL
+    plan.destroy()
+
+
 # ---------------------------------------------------------------------------
-# the DFT itself at any length (Bluestein on the power-of-two engine)
+# the DFT itself at any length (the mixed-radix engine at 7-smooth lengths,
+# Bluestein on the power-of-two engine at the others)
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("n", [2, 3, 5, 100, 127, 128, 255, 1000, 3000, 5000, 8191])
@@ -205,7 +236,7 @@ def test_fft_any_length_vs_oracle(sar, orc, n, inverse):
     torch.cuda.synchronize()
     got = out.cpu().numpy()
     err = M.rel_l2(got, ref)
-    print(f"\nBLUESTEIN n={n} {'inv' if inverse else 'fwd'}: rel_l2 {err:.2e}")
+    print(f"\nDFT n={n} {'inv' if inverse else 'fwd'}: rel_l2 {err:.2e}")
     assert err < 2e-6
     assert np.array_equal(xd.cpu().numpy(), x.astype(np.complex64))
     sar.sar_fft_lines(n, 3, xd, xd, inverse)                     # in place
