@@ -555,7 +555,7 @@ def any_length_bench(sar, dev, stream, peak, reps: int = 20) -> dict:
         out[str(n)] = {"engine_length": L, "schedule": sched["name"], "lines": n_lines, "ms": ms, "gb_s": gbs,
                        "frac_hbm": gbs / peak}
         plan.destroy()
-        # the DFT alone at the same length (Bluestein when n is not a power of two)
+        # the DFT alone at the same length (mixed radix at 7-smooth n, Bluestein at other non-powers of two)
         times = []
         for i in range(reps + 3):
             e0.record(stream)
