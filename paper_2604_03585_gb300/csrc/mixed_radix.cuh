@@ -413,6 +413,10 @@ typedef cudaError_t (*mixed3_dft_fn)(const float2*, float2*, int64_t, int64_t, i
                                      cudaStream_t);
 mixed3_fn specialised(const MixedGeom& g);
 mixed3_dft_fn specialised_dft(const MixedGeom& g);
+// the second table (mixed_radix_ct2.cu), consulted by the two above
+mixed3_fn specialised_more(const MixedGeom& g);
+mixed3_dft_fn specialised_dft_more(const MixedGeom& g);
+cudaError_t prepare_specialised_more();
 cudaError_t prepare_specialised();
 
 }  // namespace mixed

@@ -93,7 +93,7 @@ def test_line_compression_any_length(sar, orc, n, lines):
 # lengths with a compile-time specialisation of the mixed-radix kernel; lines
 # span several blocks and end in a partial one
 @pytest.mark.parametrize("n,lines", [(1000, 13), (2000, 7), (3000, 5), (4000, 5), (5000, 3), (6000, 3),
-                                     (8000, 3)])
+                                     (8000, 3), (1200, 9), (1500, 5), (2400, 3), (3500, 2), (4800, 2), (7200, 2)])
 def test_specialised_mixed_kernel_equals_runtime_kernel(sar, n, lines, monkeypatch):
     """The kernels compiled for one length and the runtime-radix kernels run
     the same passes on the same tables: bit-identical results, for the fused
