@@ -383,6 +383,16 @@ typedef struct {
  * item advancing together), while the per-class kernels run four or five
  * blocks per SM. */
 #define SAR_BATCH_MULTI_KERNEL 2u
+/* With SAR_BATCH_MULTI_KERNEL (or SAR_BATCH_EXACT_AZIMUTH): before the graph
+ * is captured, time every compiled schedule of each class's power-of-two
+ * length (sar_autotune, kind SAR_TUNE_FUSED, 5 repetitions on up to 2^24
+ * samples of lines; allocates and synchronises) and give the class the
+ * fastest one that has a segment-table kernel (as after sar_autotune, the
+ * fastest schedule of each length also becomes its preferred one); without it
+ * a class takes the preferred schedule of its length.  Refused
+ * (SAR_ERR_INVALID_ARG) for the one-launch kernel, whose line engines are
+ * compiled in. */
+#define SAR_BATCH_AUTOTUNE 4u
 SAR_API sar_status sar_batch_create(const sar_strip *strips, int32_t count, uint32_t flags, sar_batch *out);
 
 /* Compress every strip of the batch: one graph launch on `stream`;

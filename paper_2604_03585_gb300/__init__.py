@@ -30,6 +30,7 @@ SAR_PLAN_UNFOLDED_CORNER_TURN = 1
 SAR_PLAN_OUT_AZ_MAJOR = 2
 SAR_BATCH_EXACT_AZIMUTH = 1
 SAR_BATCH_MULTI_KERNEL = 2
+SAR_BATCH_AUTOTUNE = 4
 SAR_TUNE_FUSED, SAR_TUNE_RANGE_CT = 0, 1
 SAR_SERVE_OPEN_LOOP, SAR_SERVE_CLOSED_LOOP = 0, 1
 

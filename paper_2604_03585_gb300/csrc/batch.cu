@@ -109,6 +109,31 @@ const SchedDesc *seg_schedule(int n) {
     return nullptr;
 }
 
+// SAR_BATCH_AUTOTUNE: the fastest schedule of length n that has a
+// segment-table kernel, timed by sar_autotune on `lines` lines of n (every
+// compiled schedule of n; the medians come back in the registry's order of
+// the schedules of n).  nullptr on any failure (the caller then keeps the
+// preferred schedule).
+const SchedDesc *tuned_seg_schedule(int n, int64_t lines) {
+    std::vector<const SchedDesc *> of_n;
+    for (int i = 0; i < sar::schedule_count(); ++i)
+        if (sar::schedule_at(i)->n == n) of_n.push_back(sar::schedule_at(i));
+    if (of_n.empty()) return nullptr;
+    std::vector<float> ms(of_n.size(), 0.f);
+    sar_schedule_desc best;
+    float best_ms = 0.f;
+    if (sar_autotune(n, lines, 5, SAR_TUNE_FUSED, nullptr, &best, &best_ms, ms.data(), (int32_t)ms.size()) != SAR_OK)
+        return nullptr;
+    const SchedDesc *win = nullptr;
+    float win_ms = 0.f;
+    for (size_t i = 0; i < of_n.size(); ++i)
+        if (of_n[i]->fused_seg && ms[i] > 0.f && (!win || ms[i] < win_ms)) {
+            win = of_n[i];
+            win_ms = ms[i];
+        }
+    return win;
+}
+
 }  // namespace
 
 struct sar_batch_s {
@@ -309,10 +334,14 @@ sar_status sar_batch_create(const sar_strip *strips, int32_t count, uint32_t fla
     if (!out) return sar::report_error(SAR_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!strips || count < 1) return sar::report_error(SAR_ERR_INVALID_ARG, "need at least one strip");
-    if (flags & ~(SAR_BATCH_EXACT_AZIMUTH | SAR_BATCH_MULTI_KERNEL))
+    if (flags & ~(SAR_BATCH_EXACT_AZIMUTH | SAR_BATCH_MULTI_KERNEL | SAR_BATCH_AUTOTUNE))
         return sar::report_error(SAR_ERR_INVALID_ARG, "unknown flags");
     const bool exact = (flags & SAR_BATCH_EXACT_AZIMUTH) != 0;
     const bool multi = exact || (flags & SAR_BATCH_MULTI_KERNEL) != 0;
+    const bool tune = (flags & SAR_BATCH_AUTOTUNE) != 0;
+    if (tune && !multi)
+        return sar::report_error(SAR_ERR_INVALID_ARG,
+                                 "SAR_BATCH_AUTOTUNE needs the multi-kernel graph (the one-launch kernel's engines are fixed)");
     sar_status st;
     for (int32_t i = 0; i < count; ++i) {
         const sar_strip &s = strips[i];
@@ -389,7 +418,12 @@ sar_status sar_batch_create(const sar_strip *strips, int32_t count, uint32_t fla
                 while (L < 2 * c.n - 1) L <<= 1;
                 c.d = sar::wrap_schedule((int)L);
             } else {
-                c.d = seg_schedule((int)c.n);
+                c.d = nullptr;
+                if (tune) {
+                    const int64_t lines = c.begin.back() < (1 << 24) / c.n ? c.begin.back() : (1 << 24) / c.n;
+                    c.d = tuned_seg_schedule((int)c.n, lines > 0 ? lines : 1);
+                }
+                if (!c.d) c.d = seg_schedule((int)c.n);
             }
             if (!c.d) {
                 batch_free(b);

@@ -238,3 +238,31 @@ def test_ragged_batch_exact_azimuth_vs_oracle(sar):
         sar.sar_batch_create([dict(n_range=256, n_az=9000, raw=x, image=x, range_spectrum=x, az_spectrum=x)],
                              flags=sar.SAR_BATCH_EXACT_AZIMUTH)
     assert e.value.status == sar.SAR_ERR_UNSUPPORTED
+
+
+def test_multi_kernel_graph_autotuned_vs_oracle(sar):
+    """SAR_BATCH_AUTOTUNE times every schedule of each class's length at batch
+    creation and gives the class the fastest with a segment-table kernel; the
+    images still match the oracle.  Refused for the one-launch kernel."""
+    orc = oracle.default()
+    shapes = [(1024, 200), (2048, 129), (512, 256), (1024, 77)]
+    strips, keep, specs, hr, ha = make_strips(sar, orc, shapes, seed=12)
+    with pytest.raises(sar.SarError) as e:
+        sar.sar_batch_create(strips, flags=sar.SAR_BATCH_AUTOTUNE)
+    assert e.value.status == sar.SAR_ERR_INVALID_ARG
+    batch = sar.sar_batch_create(strips, flags=sar.SAR_BATCH_MULTI_KERNEL | sar.SAR_BATCH_AUTOTUNE)
+    try:
+        assert sar.sar_batch_info(batch)["kernels_per_run"] > 1
+        sar.sar_batch_run(batch)
+        sar.sar_sync()
+        for (raw, raw_d, img_d), spec in zip(keep, specs):
+            Hr = hr[spec.n_range].cpu().numpy().astype(np.complex128)
+            Ha = ha[spec.l_az].cpu().numpy().astype(np.complex128)
+            ref = orc.rda(raw, Hr, Ha, l_az=spec.l_az, nthreads=NTHREADS)
+            assert M.rel_l2(img_d.cpu().numpy(), ref) < 2e-5, (spec.n_range, spec.n_az)
+    finally:
+        batch.destroy()
+        # the tuning made its winners the preferred schedules: back to the
+        # compiled defaults (the first schedule of each length)
+        for n in (256, 512, 1024, 2048):
+            sar.sar_set_preferred_schedule(sar.schedules(n)[0]["name"])
