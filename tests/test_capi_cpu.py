@@ -117,3 +117,28 @@ def test_bench_refuses_unknown_extras(monkeypatch):
     every = set(bench.parse().extras.split(","))
     assert {"passes", "scene_256", "pipelined", "az_major", "unfused", "precision", "rda_full", "long_lines",
             "any_length", "ragged_batch", "serving"} == every
+
+
+def test_traffic_record_scope_and_hash(tmp_path):
+    """The recorded ncu traffic is tied to the sources of the kernels it was
+    taken from: the 4096-point schedule table and every csrc header it
+    includes, followed through nested includes; a change to one of them
+    changes the hash, a change elsewhere does not."""
+    from paper_2604_03585_gb300 import roofline
+    import os
+    csrc = os.path.join(os.path.dirname(roofline.__file__), "csrc")
+    seen = set()
+    roofline._local_includes(os.path.join(csrc, "sched_4096.cu"), seen)
+    names = {os.path.basename(f) for f in seen}
+    assert {"sched_4096.cu", "launch.cuh", "streamed.cuh", "line_engine.cuh", "sar_common.cuh"} <= names
+    assert "mixed_radix.cuh" not in names and "cluster_line.cu" not in names
+    # nested includes on a scratch tree
+    (tmp_path / "a.cu").write_text('#include "b.cuh"\n')
+    (tmp_path / "b.cuh").write_text('#pragma once\n#include "c.h"\n')
+    (tmp_path / "c.h").write_text("int x;\n")
+    (tmp_path / "d.h").write_text("int y;\n")
+    seen = set()
+    roofline._local_includes(str(tmp_path / "a.cu"), seen)
+    assert {os.path.basename(f) for f in seen} == {"a.cu", "b.cuh", "c.h"}
+    h = roofline.kernel_source_hash()
+    assert len(h) == 16 and h == roofline.kernel_source_hash()
