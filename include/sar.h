@@ -64,7 +64,7 @@ typedef struct sar_plan_s *sar_plan; /* opaque; immutable after creation; usable
 typedef enum {
     SAR_OK = 0,
     SAR_ERR_INVALID_ARG = 1,   /* null/misaligned pointer, size out of range, bad flag */
-    SAR_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement (e.g. N > 131072) */
+    SAR_ERR_UNSUPPORTED = 2,   /* valid request the library does not implement (e.g. N > 131072) */
     SAR_ERR_OUT_OF_MEMORY = 3, /* a plan allocation failed; nothing was leaked */
     SAR_ERR_CUDA = 4,          /* a CUDA runtime call or launch failed */
     SAR_ERR_TIMEOUT = 5        /* a bounded device-side wait gave up */

@@ -418,5 +418,5 @@ int oracle_rda_full(int64_t n_az, int64_t n_range, const cplx *raw, const cplx *
     return st ? -1 : 0;
 }
 
-/* Which planted mistake this build carries (0 = none). */
+/* Which planted mistake this compiled copy of the oracle carries (0 = none). */
 int oracle_planted(void) { return ORACLE_PLANT; }
