@@ -302,7 +302,8 @@ sar_status sar_plan_create_ex(int64_t n_range, int64_t n_az, const sar_filters *
     if ((st = check_device_ptr(filters->range_spectrum, "filters->range_spectrum")) != SAR_OK) return st;
     if ((st = check_device_ptr(filters->az_spectrum, "filters->az_spectrum")) != SAR_OK) return st;
 
-    const bool want_fold = !(filters->flags & SAR_PLAN_UNFOLDED_CORNER_TURN) && prec == SAR_PREC_FP32 && !wrap_r;
+    const bool want_fold = !(filters->flags & SAR_PLAN_UNFOLDED_CORNER_TURN) && prec == SAR_PREC_FP32 &&
+                           (!wrap_r || sar::mixed_length((int)n_range));
     const SchedDesc *dr = range_schedule ? sar::find_schedule(range_schedule) : nullptr;
     if (wrap_r) {
         dr = sar::mixed_length((int)n_range) ? sar::mixed_schedule((int)n_range)

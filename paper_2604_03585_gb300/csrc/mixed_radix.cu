@@ -172,6 +172,20 @@ cudaError_t launch_mixed_dft(const float2* in, float2* out, int64_t n_lines, int
     return launch_dft_mixed(in, out, n_lines, ld, valid, tw, inverse, g, lines_per_block(g), smem_bytes(g), st);
 }
 
+// the folded range pass of the plan's length (fused_ct of the descriptor):
+// the compiled kernel of its length, which exists when the descriptor
+// offers this entry.  One entry serves every mixed length, so the length is
+// taken from ld_in: raw rows are contiguous lines of n samples on every
+// caller of fused_ct.
+cudaError_t launch_mixed_ct(const float2* in, float2* img, int64_t n_lines, int64_t ld_in, int64_t ld_img,
+                            const float2* filt, const float2* tw, cudaStream_t st) {
+    MixedGeom g{};
+    if (!geometry((int)ld_in, g)) return cudaErrorInvalidValue;
+    const mixed3_ct_fn f = specialised_ct(g);
+    if (!f) return cudaErrorInvalidValue;
+    return f(in, img, n_lines, ld_in, ld_img, filt, tw, st);
+}
+
 cudaError_t prepare_mixed() {
     cudaError_t e = set_smem_k2(kMixedSmemMax);
     if (e == cudaSuccess) e = set_smem_k3(kMixedSmemMax);
@@ -208,6 +222,10 @@ const SchedDesc* mixed_schedule(int n) {
                         lines_per_block(g), kMixedThreads, smem_bytes(g), twiddle_elems(g), g.R[g.P - 1], 0,
                         &launch_mixed, &launch_mixed_dft, &prepare_mixed, nullptr, 0, nullptr, 0};
     e->desc.mixed = 1;
+    if (specialised_ct(g)) {   // the folded range pass: clusters of four lines
+        e->desc.fused_ct = &launch_mixed_ct;
+        e->desc.ct_lines = 4;
+    }
     g_descs[n] = e;
     return &e->desc;
 }

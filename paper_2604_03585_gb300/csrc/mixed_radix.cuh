@@ -2,6 +2,7 @@
 // register DFTs of every radix, the pass routines and the fused kernel.
 #pragma once
 
+#include <cooperative_groups.h>
 #include <utility>
 
 #include "launch.cuh"
@@ -376,6 +377,82 @@ mixed3_dft_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld, in
         }
 }
 
+// The fused compression of a compiled length with the corner turn folded
+// into its store (Sec. IV-A steps 1 and 2 in one kernel), for lengths run with
+// one line per block: a cluster of four blocks compresses four consecutive
+// range lines.  The forward passes, the filter and the inverse middle passes
+// are those of fused_mixed3_kernel; the inverse first pass keeps its results
+// in registers, and after a cluster barrier each block pushes natural-order
+// sample i of its line into the shared memory of block i / (N/4), row
+// `rank` (padded by 4 slots, as the power-of-two fold), slot i mod (N/4).
+// After a second barrier each block writes each of its N/4 range bins' four
+// samples as one 32-byte run of image row i.  Same arithmetic as the
+// unfolded kernel and the separate corner turn: bit-identical images.
+template <int N, int RA, int RB, int RC, int MINB, int PADDIV>
+__global__ void __launch_bounds__(kMixedThreads, MINB)
+fused_mixed3_ct_kernel(const float2* in, float2* img, int64_t ld_in, int64_t ld_img, const float2* filt,
+                       const float2* tw) {
+    namespace cg = cooperative_groups;
+    constexpr int T = kMixedThreads;
+    constexpr int SA = N / RA, SB = SA / RB;
+    static_assert(RA * RB * RC == N && SB == RC, "three radices of N");
+    constexpr uint32_t MA = split_magic(SA), MB = split_magic(SB);
+    constexpr int PADN = mixed3_smem<N, T, PADDIV>() / (int)sizeof(float2);
+    constexpr int QC = 4, NQ = N / QC, RS = NQ + 4, GA = (SA + T - 1) / T;
+    static_assert(N % QC == 0 && QC * RS <= PADN, "four receive rows fit the line buffer");
+    extern __shared__ float2 smem_mixed[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int t = threadIdx.x;
+    const int rank = (int)cluster.block_rank();
+    const int64_t line = blockIdx.x;
+    const int64_t a0 = line - rank;
+    float2* sm = smem_mixed;
+    const float2* src = in + line * ld_in;
+    const float2* twb = tw + RA * SA;
+    for (int g = t; g < N / RA; g += T) mgroup<RA, kFirst, false, PADDIV>(g, SA, MA, N / RA, src, img, sm, tw, filt);
+    __syncthreads();
+    for (int g = t; g < N / RB; g += T) mgroup<RB, kMid, false, PADDIV>(g, SB, MB, N / RB, src, img, sm, twb, filt);
+    __syncthreads();
+    for (int g = t; g < N / RC; g += T) mgroup<RC, kLast, false, PADDIV>(g, 1, 0u, N / RC, src, img, sm, tw, filt);
+    __syncthreads();
+    for (int g = t; g < N / RB; g += T)
+        mgroup<RB, kInvMid, false, PADDIV>(g, SB, MB, N / RB, src, img, sm, twb, filt);
+    __syncthreads();
+    // inverse first pass into registers: group g < SA holds positions g + r SA
+    float2 v[GA][RA];
+#pragma unroll
+    for (int s = 0; s < GA; ++s) {
+        const int g = t + T * s;
+        if (g < SA) {
+#pragma unroll
+            for (int r = 0; r < RA; ++r) v[s][r] = sm[mslot<PADDIV>(g + r * SA)];
+#pragma unroll
+            for (int r = 1; r < RA; ++r) v[s][r] = cmulc(v[s][r], tw[r * SA + g]);
+            dft_any<RA, true>(v[s]);
+        }
+    }
+    cluster.sync();   // every block is done with its shared memory
+#pragma unroll
+    for (int s = 0; s < GA; ++s) {
+        const int g = t + T * s;
+        if (g < SA) {
+#pragma unroll
+            for (int r = 0; r < RA; ++r) {
+                const int i = g + r * SA;
+                float2* dst = cluster.map_shared_rank(sm, i / NQ);
+                dst[rank * RS + i % NQ] = v[s][r];
+            }
+        }
+    }
+    cluster.sync();   // the pushes have landed; only local reads from here on
+    for (int idx = t; idx < NQ * 2; idx += T) {
+        const int j = idx >> 1, p = idx & 1;
+        const float2 c0 = sm[(2 * p) * RS + j], c1 = sm[(2 * p + 1) * RS + j];
+        __stcs(reinterpret_cast<float4*>(img + (int64_t)(rank * NQ + j) * ld_img + a0 + 2 * p),
+               make_float4(c0.x, c0.y, c1.x, c1.y));
+    }
+}
+
 // one occupancy variant of the kernel (mixed_radix_k<MINB>.cu)
 template <int MINB>
 cudaError_t launch_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld, const float2* filt,
@@ -411,11 +488,16 @@ typedef cudaError_t (*mixed3_fn)(const float2*, float2*, int64_t, int64_t, const
                                  cudaStream_t);
 typedef cudaError_t (*mixed3_dft_fn)(const float2*, float2*, int64_t, int64_t, int, const float2*, int, int,
                                      cudaStream_t);
+typedef cudaError_t (*mixed3_ct_fn)(const float2*, float2*, int64_t, int64_t, int64_t, const float2*, const float2*,
+                                    cudaStream_t);
 mixed3_fn specialised(const MixedGeom& g);
 mixed3_dft_fn specialised_dft(const MixedGeom& g);
+// the folded range pass of a compiled length run one line per block, or nullptr
+mixed3_ct_fn specialised_ct(const MixedGeom& g);
 // the second table (mixed_radix_ct2.cu), consulted by the two above
 mixed3_fn specialised_more(const MixedGeom& g);
 mixed3_dft_fn specialised_dft_more(const MixedGeom& g);
+mixed3_ct_fn specialised_ct_more(const MixedGeom& g);
 cudaError_t prepare_specialised_more();
 cudaError_t prepare_specialised();
 

@@ -40,6 +40,11 @@ mixed3_dft_fn specialised_dft(const MixedGeom& g) {
     return s ? s->launch_dft : specialised_dft_more(g);
 }
 
+mixed3_ct_fn specialised_ct(const MixedGeom& g) {
+    const Spec* s = find(g);
+    return s ? s->launch_ct : specialised_ct_more(g);
+}
+
 cudaError_t prepare_specialised() {
     for (const Spec& s : kSpecs) {
         const cudaError_t e = s.attr();

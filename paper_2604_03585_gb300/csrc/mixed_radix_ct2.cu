@@ -39,6 +39,11 @@ mixed3_dft_fn specialised_dft_more(const MixedGeom& g) {
     return s ? s->launch_dft : nullptr;
 }
 
+mixed3_ct_fn specialised_ct_more(const MixedGeom& g) {
+    const Spec* s = find_more(g);
+    return s ? s->launch_ct : nullptr;
+}
+
 cudaError_t prepare_specialised_more() {
     for (const Spec& s : kMore) {
         const cudaError_t e = s.attr();
