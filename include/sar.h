@@ -98,8 +98,8 @@ typedef struct {
 /* Plan flags.  By default sar_rda_process folds the corner turn into the
  * range pass where the range schedule supports it (two kernels, 32 bytes of
  * HBM traffic per sample; powers of two up to 16384, and the mixed-radix
- * lengths with a compiled kernel of one line per block, 3000 ... 8000, with
- * n_az a multiple of 4); this flag keeps the three separate kernels of
+ * lengths with a compiled kernel, 1000 ... 8000, with n_az a multiple of 4);
+ * this flag keeps the three separate kernels of
  * Sec. IV-A (48 bytes per sample). */
 #define SAR_PLAN_UNFOLDED_CORNER_TURN 1u
 /* Azimuth-major output: sar_rda_process_oop and sar_rda_process_host return

@@ -222,7 +222,7 @@ const SchedDesc* mixed_schedule(int n) {
                         lines_per_block(g), kMixedThreads, smem_bytes(g), twiddle_elems(g), g.R[g.P - 1], 0,
                         &launch_mixed, &launch_mixed_dft, &prepare_mixed, nullptr, 0, nullptr, 0};
     e->desc.mixed = 1;
-    if (specialised_ct(g)) {   // the folded range pass: clusters of four lines
+    if (specialised_ct(g)) {   // the folded range pass: groups of four lines
         e->desc.fused_ct = &launch_mixed_ct;
         e->desc.ct_lines = 4;
     }

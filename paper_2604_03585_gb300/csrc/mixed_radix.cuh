@@ -378,35 +378,40 @@ mixed3_dft_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld, in
 }
 
 // The fused compression of a compiled length with the corner turn folded
-// into its store (Sec. IV-A steps 1 and 2 in one kernel), for lengths run with
-// one line per block: a cluster of four blocks compresses four consecutive
-// range lines.  The forward passes, the filter and the inverse middle passes
-// are those of fused_mixed3_kernel; the inverse first pass keeps its results
-// in registers, and after a cluster barrier each block pushes natural-order
-// sample i of its line into the shared memory of block i / (N/4), row
-// `rank` (padded by 4 slots, as the power-of-two fold), slot i mod (N/4).
-// After a second barrier each block writes each of its N/4 range bins' four
-// samples as one 32-byte run of image row i.  Same arithmetic as the
-// unfolded kernel and the separate corner turn: bit-identical images.
-template <int N, int RA, int RB, int RC, int MINB, int PADDIV>
+// into its store (Sec. IV-A steps 1 and 2 in one kernel): four consecutive
+// range lines per group, LPB = 256 / T lines per block and QC = 4 / LPB blocks
+// per thread-block cluster (one block of four lines for T = 64, clusters of
+// two blocks of two for T = 128, of four blocks of one for T = 256).  The
+// forward passes, the filter and the inverse middle passes are those of
+// fused_mixed3_kernel; the inverse first pass keeps its results in
+// registers, and after a barrier (the cluster's, or the block's when QC = 1)
+// each line pushes natural-order sample i into the shared memory of block
+// i / (N / QC), row = the line's place in the group (rows padded by 4 slots,
+// as the power-of-two fold), slot i mod (N / QC).  After a second barrier
+// each block writes each of its range bins' four samples as one 32-byte run
+// of image row i.  Same arithmetic as the unfolded kernel and the separate
+// corner turn: bit-identical images.
+template <int N, int RA, int RB, int RC, int T, int MINB, int PADDIV>
 __global__ void __launch_bounds__(kMixedThreads, MINB)
 fused_mixed3_ct_kernel(const float2* in, float2* img, int64_t ld_in, int64_t ld_img, const float2* filt,
                        const float2* tw) {
     namespace cg = cooperative_groups;
-    constexpr int T = kMixedThreads;
+    constexpr int LPB = kMixedThreads / T, QC = 4 / LPB;
+    static_assert(LPB * QC == 4, "groups of four lines");
     constexpr int SA = N / RA, SB = SA / RB;
     static_assert(RA * RB * RC == N && SB == RC, "three radices of N");
     constexpr uint32_t MA = split_magic(SA), MB = split_magic(SB);
-    constexpr int PADN = mixed3_smem<N, T, PADDIV>() / (int)sizeof(float2);
-    constexpr int QC = 4, NQ = N / QC, RS = NQ + 4, GA = (SA + T - 1) / T;
-    static_assert(N % QC == 0 && QC * RS <= PADN, "four receive rows fit the line buffer");
+    constexpr int PADN = mixed3_smem<N, T, PADDIV>() / LPB / (int)sizeof(float2);
+    constexpr int NQ = N / QC, RS = NQ + 4, GA = (SA + T - 1) / T;
+    static_assert(N % QC == 0 && 4 * RS <= LPB * PADN, "four receive rows fit the block's line buffers");
     extern __shared__ float2 smem_mixed[];
-    cg::cluster_group cluster = cg::this_cluster();
-    const int t = threadIdx.x;
-    const int rank = (int)cluster.block_rank();
-    const int64_t line = blockIdx.x;
-    const int64_t a0 = line - rank;
-    float2* sm = smem_mixed;
+    const int lib = threadIdx.x / T, t = threadIdx.x % T;
+    int rank = 0;
+    if constexpr (QC > 1) rank = (int)cg::this_cluster().block_rank();
+    const int64_t a0 = ((int64_t)blockIdx.x - rank) * LPB;   // first line of the group of four
+    const int row = rank * LPB + lib;                         // this line's place in the group
+    const int64_t line = a0 + row;
+    float2* sm = smem_mixed + lib * PADN;
     const float2* src = in + line * ld_in;
     const float2* twb = tw + RA * SA;
     for (int g = t; g < N / RA; g += T) mgroup<RA, kFirst, false, PADDIV>(g, SA, MA, N / RA, src, img, sm, tw, filt);
@@ -431,7 +436,10 @@ fused_mixed3_ct_kernel(const float2* in, float2* img, int64_t ld_in, int64_t ld_
             dft_any<RA, true>(v[s]);
         }
     }
-    cluster.sync();   // every block is done with its shared memory
+    if constexpr (QC > 1)
+        cg::this_cluster().sync();   // every block is done with its shared memory
+    else
+        __syncthreads();
 #pragma unroll
     for (int s = 0; s < GA; ++s) {
         const int g = t + T * s;
@@ -439,15 +447,19 @@ fused_mixed3_ct_kernel(const float2* in, float2* img, int64_t ld_in, int64_t ld_
 #pragma unroll
             for (int r = 0; r < RA; ++r) {
                 const int i = g + r * SA;
-                float2* dst = cluster.map_shared_rank(sm, i / NQ);
-                dst[rank * RS + i % NQ] = v[s][r];
+                float2* dst = smem_mixed;
+                if constexpr (QC > 1) dst = cg::this_cluster().map_shared_rank(smem_mixed, i / NQ);
+                dst[row * RS + i % NQ] = v[s][r];
             }
         }
     }
-    cluster.sync();   // the pushes have landed; only local reads from here on
-    for (int idx = t; idx < NQ * 2; idx += T) {
+    if constexpr (QC > 1)
+        cg::this_cluster().sync();   // the pushes have landed; only local reads from here on
+    else
+        __syncthreads();
+    for (int idx = threadIdx.x; idx < NQ * 2; idx += kMixedThreads) {
         const int j = idx >> 1, p = idx & 1;
-        const float2 c0 = sm[(2 * p) * RS + j], c1 = sm[(2 * p + 1) * RS + j];
+        const float2 c0 = smem_mixed[(2 * p) * RS + j], c1 = smem_mixed[(2 * p + 1) * RS + j];
         __stcs(reinterpret_cast<float4*>(img + (int64_t)(rank * NQ + j) * ld_img + a0 + 2 * p),
                make_float4(c0.x, c0.y, c1.x, c1.y));
     }
@@ -492,7 +504,7 @@ typedef cudaError_t (*mixed3_ct_fn)(const float2*, float2*, int64_t, int64_t, in
                                     cudaStream_t);
 mixed3_fn specialised(const MixedGeom& g);
 mixed3_dft_fn specialised_dft(const MixedGeom& g);
-// the folded range pass of a compiled length run one line per block, or nullptr
+// the folded range pass of a compiled length, or nullptr
 mixed3_ct_fn specialised_ct(const MixedGeom& g);
 // the second table (mixed_radix_ct2.cu), consulted by the two above
 mixed3_fn specialised_more(const MixedGeom& g);

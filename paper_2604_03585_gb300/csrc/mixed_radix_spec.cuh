@@ -24,31 +24,28 @@ cudaError_t launch3_dft(const float2* in, float2* out, int64_t n_lines, int64_t 
         in, out, n_lines, ld, valid, tw, pos_off, inverse ? -1.f : 1.f);
     return cudaGetLastError();
 }
-// the folded range pass (lengths run one line per block): clusters of four
-// blocks over n_lines (a multiple of 4) lines
+// the folded range pass: groups of four lines over n_lines (a multiple of
+// 4), 256 / T lines per block, clusters of 4 T / 256 blocks (none for T = 64)
 template <int N, int RA, int RB, int RC, int T, int MINB, int PD>
 cudaError_t launch3_ct(const float2* in, float2* img, int64_t n_lines, int64_t ld_in, int64_t ld_img,
                        const float2* filt, const float2* tw, cudaStream_t st) {
-    if constexpr (T != kMixedThreads) {
-        return cudaErrorInvalidValue;
-    } else {
-        if (n_lines <= 0) return cudaSuccess;
-        if (n_lines % 4 || ld_img % 2) return cudaErrorInvalidValue;
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)n_lines, 1, 1);
-        cfg.blockDim = dim3(kMixedThreads, 1, 1);
-        cfg.dynamicSmemBytes = mixed3_smem<N, T, PD>();
-        cfg.stream = st;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = 4;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, fused_mixed3_ct_kernel<N, RA, RB, RC, MINB, PD>, in, img, ld_in, ld_img, filt,
-                                  tw);
-    }
+    constexpr int LPB = kMixedThreads / T, QC = 4 / LPB;
+    if (n_lines <= 0) return cudaSuccess;
+    if (n_lines % 4 || ld_img % 2) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(n_lines / LPB), 1, 1);
+    cfg.blockDim = dim3(kMixedThreads, 1, 1);
+    cfg.dynamicSmemBytes = mixed3_smem<N, T, PD>();
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = QC;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = QC > 1 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, fused_mixed3_ct_kernel<N, RA, RB, RC, T, MINB, PD>, in, img, ld_in, ld_img, filt,
+                              tw);
 }
 template <int N, int RA, int RB, int RC, int T, int MINB, int PD>
 cudaError_t attr3() {
@@ -57,10 +54,9 @@ cudaError_t attr3() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(mixed3_dft_kernel<N, RA, RB, RC, T, MINB, PD>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kMixedSmemMax);
-    if constexpr (T == kMixedThreads)
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(fused_mixed3_ct_kernel<N, RA, RB, RC, MINB, PD>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kMixedSmemMax);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fused_mixed3_ct_kernel<N, RA, RB, RC, T, MINB, PD>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kMixedSmemMax);
     return e;
 }
 
@@ -68,12 +64,12 @@ struct Spec {
     int n, ra, rb, rc, t, minb;
     mixed3_fn launch;
     mixed3_dft_fn launch_dft;
-    mixed3_ct_fn launch_ct;   // nullptr below one line per block
+    mixed3_ct_fn launch_ct;
     cudaError_t (*attr)();
 };
 #define SAR_SPEC(N, RA, RB, RC, T, MB, PD)                                                                 \
     Spec{N, RA, RB, RC, T, MB, &launch3<N, RA, RB, RC, T, MB, PD>, &launch3_dft<N, RA, RB, RC, T, MB, PD>,  \
-         (T == kMixedThreads ? &launch3_ct<N, RA, RB, RC, T, MB, PD> : nullptr), &attr3<N, RA, RB, RC, T, MB, PD>}
+         &launch3_ct<N, RA, RB, RC, T, MB, PD>, &attr3<N, RA, RB, RC, T, MB, PD>}
 
 }  // namespace mixed
 }  // namespace sar
