@@ -5,6 +5,7 @@
 #include "persistent.cuh"
 #include "streamed.cuh"
 #include "registry.h"
+#include "tensor_map.h"
 
 namespace sar {
 
@@ -181,6 +182,13 @@ cudaError_t prepare_streamed() {
                                      cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
             if (e != cudaSuccess) return e;
         }
+        if constexpr (ct_tma_ok<SC, QC, ROLL>()) {
+            if (smem_bytes_of<SC, 1>() > 48 * 1024) {
+                e = cudaFuncSetAttribute(fused_range_ct_tma_kernel<SC, QC, ROLL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes_of<SC, 1>());
+                if (e != cudaSuccess) return e;
+            }
+        }
     }
     return prepare_sched<SC, 1>();
 }
@@ -227,6 +235,12 @@ cudaError_t launch_range_ct_cluster(const float2 *in, float2 *img, int64_t n_lin
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if constexpr (ct_tma_ok<SC, QC, ROLL>()) {
+        CUtensorMap m;
+        if (image_tensor_map(&m, img, n_lines, SC::N, ld_img, 1, 256))
+            return cudaLaunchKernelEx(&cfg, fused_range_ct_tma_kernel<SC, QC, ROLL>, in, img, m, ld_in, ld_img, filt,
+                                      tw);
+    }
     return cudaLaunchKernelEx(&cfg, fused_range_ct_cluster_kernel<SC, QC, ROLL>, in, img, ld_in, ld_img, filt, tw);
 }
 

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cooperative_groups.h>
+#include <cuda.h>
 #include <utility>
 
 #include "launch.cuh"
@@ -391,10 +392,28 @@ mixed3_dft_kernel(const float2* in, float2* out, int64_t n_lines, int64_t ld, in
 // each block writes each of its range bins' four samples as one 32-byte run
 // of image row i.  Same arithmetic as the unfolded kernel and the separate
 // corner turn: bit-identical images.
-template <int N, int RA, int RB, int RC, int T, int MINB, int PADDIV>
-__global__ void __launch_bounds__(kMixedThreads, MINB)
-fused_mixed3_ct_kernel(const float2* in, float2* img, int64_t ld_in, int64_t ld_img, const float2* filt,
-                       const float2* tw) {
+template <int N, int T, int PADDIV>
+struct MixedCtGeom {
+    static constexpr int LPB = kMixedThreads / T, QC = 4 / LPB;
+    static constexpr int PADN = mixed3_smem<N, T, PADDIV>() / LPB / (int)sizeof(float2);
+    static constexpr int NQ = N / QC, RS = NQ + 4;
+    static constexpr int CAP = LPB * PADN;   // float2 of shared memory per block
+    // tensor-store boxes: NB boxes of BR bin rows (BR a multiple of 4, so that
+    // every box starts 128 bytes aligned; NB BR >= NQ, the last box clipped at
+    // the block's plane), staged bin-major in the block's shared memory
+    __host__ __device__ static constexpr int box_rows(int nb) { return ((NQ + nb - 1) / nb + 3) / 4 * 4; }
+    __host__ __device__ static constexpr int boxes() {
+        int nb = (NQ + 255) / 256;
+        while (box_rows(nb) > 256 || nb * box_rows(nb) * 4 > CAP) ++nb;
+        return nb;
+    }
+    static constexpr int NB = boxes(), BR = box_rows(NB);
+    static constexpr int NIT = (2 * NQ + kMixedThreads - 1) / kMixedThreads;   // float4 staged per thread
+};
+
+template <int N, int RA, int RB, int RC, int T, int MINB, int PADDIV, bool TMA>
+__device__ __forceinline__ void fused_mixed3_ct_body(const float2* in, float2* img, int64_t ld_in, int64_t ld_img,
+                                                     const float2* filt, const float2* tw, const CUtensorMap* tmap) {
     namespace cg = cooperative_groups;
     constexpr int LPB = kMixedThreads / T, QC = 4 / LPB;
     static_assert(LPB * QC == 4, "groups of four lines");
@@ -457,12 +476,72 @@ fused_mixed3_ct_kernel(const float2* in, float2* img, int64_t ld_in, int64_t ld_
         cg::this_cluster().sync();   // the pushes have landed; only local reads from here on
     else
         __syncthreads();
+    if constexpr (TMA) {
+        // the receive rows rewritten bin-major in place (bin j's four samples
+        // at stg[2j], stg[2j + 1]) and stored as NB boxes of the block's plane
+        using G = MixedCtGeom<N, T, PADDIV>;
+        float4 w[G::NIT];
+#pragma unroll
+        for (int k = 0; k < G::NIT; ++k) {
+            const int idx = threadIdx.x + k * kMixedThreads, j = idx >> 1, p = idx & 1;
+            if (idx < NQ * 2) {
+                const float2 c0 = smem_mixed[(2 * p) * RS + j], c1 = smem_mixed[(2 * p + 1) * RS + j];
+                w[k] = make_float4(c0.x, c0.y, c1.x, c1.y);
+            }
+        }
+        __syncthreads();
+        float4* stg = reinterpret_cast<float4*>(smem_mixed);
+        const uint32_t base = (uint32_t)__cvta_generic_to_shared(stg);
+        if (base & 127) {   // a tensor copy wants 128-byte aligned shared memory: plain stores
+#pragma unroll
+            for (int k = 0; k < G::NIT; ++k) {
+                const int idx = threadIdx.x + k * kMixedThreads, j = idx >> 1, p = idx & 1;
+                if (idx < NQ * 2)
+                    __stcs(reinterpret_cast<float4*>(img + (int64_t)(rank * NQ + j) * ld_img + a0 + 2 * p), w[k]);
+            }
+            return;
+        }
+#pragma unroll
+        for (int k = 0; k < G::NIT; ++k) {
+            const int idx = threadIdx.x + k * kMixedThreads;
+            if (idx < NQ * 2) stg[idx] = w[k];
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+#pragma unroll 1
+            for (int c = 0; c < G::NB; ++c)
+                asm volatile(
+                    "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(tmap),
+                    "r"(base + c * G::BR * 32), "r"((int)(2 * a0)), "r"(c * G::BR), "r"(rank)
+                    : "memory");
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        }
+        return;
+    }
     for (int idx = threadIdx.x; idx < NQ * 2; idx += kMixedThreads) {
         const int j = idx >> 1, p = idx & 1;
         const float2 c0 = smem_mixed[(2 * p) * RS + j], c1 = smem_mixed[(2 * p + 1) * RS + j];
         __stcs(reinterpret_cast<float4*>(img + (int64_t)(rank * NQ + j) * ld_img + a0 + 2 * p),
                make_float4(c0.x, c0.y, c1.x, c1.y));
     }
+}
+
+template <int N, int RA, int RB, int RC, int T, int MINB, int PADDIV>
+__global__ void __launch_bounds__(kMixedThreads, MINB)
+fused_mixed3_ct_kernel(const float2* in, float2* img, int64_t ld_in, int64_t ld_img, const float2* filt,
+                       const float2* tw) {
+    fused_mixed3_ct_body<N, RA, RB, RC, T, MINB, PADDIV, false>(in, img, ld_in, ld_img, filt, tw, nullptr);
+}
+
+// the same fold with the image tiles written by tensor stores (tmap: the
+// image as one plane of N / QC bin rows per block of a cluster)
+template <int N, int RA, int RB, int RC, int T, int MINB, int PADDIV>
+__global__ void __launch_bounds__(kMixedThreads, MINB)
+fused_mixed3_ct_tma_kernel(const float2* in, float2* img, const __grid_constant__ CUtensorMap tmap, int64_t ld_in,
+                           int64_t ld_img, const float2* filt, const float2* tw) {
+    fused_mixed3_ct_body<N, RA, RB, RC, T, MINB, PADDIV, true>(in, img, ld_in, ld_img, filt, tw, &tmap);
 }
 
 // one occupancy variant of the kernel (mixed_radix_k<MINB>.cu)

@@ -3,6 +3,7 @@
 #pragma once
 
 #include "mixed_radix.cuh"
+#include "tensor_map.h"
 
 namespace sar {
 namespace mixed {
@@ -44,6 +45,11 @@ cudaError_t launch3_ct(const float2* in, float2* img, int64_t n_lines, int64_t l
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = QC > 1 ? 1 : 0;
+    using G = MixedCtGeom<N, T, PD>;
+    CUtensorMap m;
+    if (image_tensor_map(&m, img, n_lines, N, ld_img, QC, G::BR))
+        return cudaLaunchKernelEx(&cfg, fused_mixed3_ct_tma_kernel<N, RA, RB, RC, T, MINB, PD>, in, img, m, ld_in,
+                                  ld_img, filt, tw);
     return cudaLaunchKernelEx(&cfg, fused_mixed3_ct_kernel<N, RA, RB, RC, T, MINB, PD>, in, img, ld_in, ld_img, filt,
                               tw);
 }
@@ -56,6 +62,9 @@ cudaError_t attr3() {
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kMixedSmemMax);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(fused_mixed3_ct_kernel<N, RA, RB, RC, T, MINB, PD>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kMixedSmemMax);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fused_mixed3_ct_tma_kernel<N, RA, RB, RC, T, MINB, PD>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kMixedSmemMax);
     return e;
 }
