@@ -287,6 +287,23 @@ def test_transpose_bit_exact(sar, rows, cols):
     assert torch.equal(y, x.t().contiguous())
 
 
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("rows,cols", [(4096, 4096), (128, 64), (192, 320), (100, 64), (64, 1000)])
+def test_transpose_variants_bit_exact(sar, variant, rows, cols):
+    """Both corner-turn kernels (32 x 32 tiles of 8-byte accesses; 64 x 64
+    tiles of 16-byte accesses where rows and columns are multiples of 64,
+    the 32 x 32 kernel otherwise) move every sample exactly."""
+    x = torch.randn(rows, cols, dtype=torch.complex64, device="cuda")
+    y = empty_c64(cols, rows)
+    sar.sar_set_corner_turn_variant(variant)
+    try:
+        sar.sar_transpose(rows, cols, x, y)
+        torch.cuda.synchronize()
+    finally:
+        sar.sar_set_corner_turn_variant(0)
+    assert torch.equal(y, x.t().contiguous())
+
+
 def test_corner_turn_plan_shape(sar):
     n_az, n_r = 512, 2048
     plan = make_plan(sar, n_r, n_az, rand_c64(n_r, 1), rand_c64(n_az, 2))
