@@ -264,9 +264,10 @@ __device__ __forceinline__ void fused_range_ct_body(const float2* in, float2* im
 
 // The fold whose image tiles leave through the tensor memory accelerator:
 // after the exchange each block rewrites its receive rows bin-major in place
-// (bin j's four samples at 32 j bytes) and one thread stores them as 2-D
-// boxes of 4 azimuth samples x 256 range bins (cp.async.bulk.tensor), in
-// place of 16 rows of 32 bytes per warp store instruction.  For clusters of
+// (bin j's four samples at 32 j bytes) and one thread stores them as boxes
+// of 4 azimuth samples x 256 range bins (cp.async.bulk.tensor over the image
+// as a one-plane tensor of fp32 pairs, tensor_map.h), in place of 16 rows of
+// 32 bytes per warp store instruction.  For clusters of
 // four and the rolled E = 32 engines of up to 256 threads (the E / 2 staged
 // float4 take the registers of the line; the unrolled and E = 16 engines run
 // the plain fold at fewer registers than this one needs, and at 16384 points,

@@ -69,19 +69,44 @@ def _local_includes(path: str, seen: set) -> None:
                 _local_includes(os.path.normpath(os.path.join(os.path.dirname(path), m.group(1))), seen)
 
 
-def kernel_source_hash() -> str:
-    """sha256 over the CUDA sources of the kernels whose traffic is recorded:
-    the 4096-point schedule table (the fused and folded range-pass kernels)
-    and every header it includes; a recorded ncu traffic figure is valid only
-    for this hash."""
+def _code_only(text: str) -> str:
+    """C/C++ source without its comments, whitespace runs collapsed to one
+    blank: what the compiler sees, so that a comment edit leaves it alone."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":                         # string or character literal, kept whole
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            out.append(" ")
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return re.sub(r"\s+", " ", "".join(out)).strip()
+
+
+def kernel_source_hash(root: str | None = None) -> str:
+    """sha256 over the code (comments and whitespace left out) of the CUDA
+    sources of the kernels whose traffic is recorded: the 4096-point schedule
+    table (the fused and folded range-pass kernels) and every header it
+    includes; a recorded ncu traffic figure is valid only for this hash.
+    `root`: the package directory to read (this one by default)."""
     h = hashlib.sha256()
     seen: set = set()
-    _local_includes(os.path.join(_HERE, "csrc", "sched_4096.cu"), seen)
-    files = sorted(seen)
-    for f in files:
+    _local_includes(os.path.join(root or _HERE, "csrc", "sched_4096.cu"), seen)
+    for f in sorted(seen):
         h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f, encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -142,3 +142,15 @@ def test_traffic_record_scope_and_hash(tmp_path):
     assert {os.path.basename(f) for f in seen} == {"a.cu", "b.cuh", "c.h"}
     h = roofline.kernel_source_hash()
     assert len(h) == 16 and h == roofline.kernel_source_hash()
+    # the hash follows the code, not its comments or layout
+    pkg = tmp_path / "pkg"
+    (pkg / "csrc").mkdir(parents=True)
+    (pkg / "csrc" / "sched_4096.cu").write_text('#include "k.cuh"\nint main_table = 1;\n')
+    (pkg / "csrc" / "k.cuh").write_text('// a kernel\nint f(int a) { return a + 1; }  /* note */\nconst char* s = "// kept";\n')
+    h0 = roofline.kernel_source_hash(str(pkg))
+    (pkg / "csrc" / "k.cuh").write_text('// the kernel, reworded\nint f(int a)   {\n  return a + 1;\n}\nconst char* s = "// kept";\n')
+    assert roofline.kernel_source_hash(str(pkg)) == h0
+    (pkg / "csrc" / "k.cuh").write_text('// a kernel\nint f(int a) { return a + 2; }\nconst char* s = "// kept";\n')
+    assert roofline.kernel_source_hash(str(pkg)) != h0
+    (pkg / "csrc" / "k.cuh").write_text('// a kernel\nint f(int a) { return a + 1; }\nconst char* s = "// changed";\n')
+    assert roofline.kernel_source_hash(str(pkg)) != h0
