@@ -258,6 +258,29 @@ def test_folded_corner_turn_matches_unfolded(sar, orc, name):
     plain.destroy()
 
 
+@pytest.mark.parametrize("n_range,n_az", [(4096, 36), (2048, 100), (8192, 12), (4096, 300), (2048, 260)])
+def test_folded_corner_turn_at_narrow_images(sar, n_range, n_az):
+    """The default folded range pass writes its image tiles as tensor-store
+    boxes of 4 azimuth samples; image rows of n_az = 4 (mod 8) samples put
+    every other box at a 16-byte (not 32-byte) offset, and widths that are
+    not powers of two run the mixed-radix or zero-padded azimuth pass.  The
+    image equals the unfolded path's with the same range schedule (the
+    default fold's) bit for bit."""
+    Hr, Ha = rand_c64(n_range, seed=11 + n_az), rand_c64(n_az, seed=12)
+    raw = rand_c64(n_az * n_range, seed=13 + n_range).reshape(n_az, n_range)
+    folded = sar.sar_plan_create(n_range, n_az, dev(Hr), dev(Ha))
+    name = sar.sar_plan_get_schedules(folded)[0]["name"]
+    plain = sar.sar_plan_create_ex(n_range, n_az, dev(Hr), dev(Ha), range_schedule=name,
+                                   flags=sar.SAR_PLAN_UNFOLDED_CORNER_TURN)
+    assert sar.sar_plan_folds_corner_turn(folded) and not sar.sar_plan_folds_corner_turn(plain)
+    i1, i2 = empty_c64(n_range, n_az), empty_c64(n_range, n_az)
+    sar.sar_rda_process(folded, dev(raw), i1)
+    sar.sar_rda_process(plain, dev(raw), i2)
+    assert np.array_equal(host(i1), host(i2))
+    folded.destroy()
+    plain.destroy()
+
+
 def test_autotune_picks_a_valid_schedule(sar):
     best, ms, allt = sar.sar_autotune(1024, 2048, reps=3)
     assert best["n"] == 1024 and ms > 0
