@@ -302,9 +302,9 @@ SAR_API sar_status sar_fft_lines(int64_t n, int64_t n_lines, const void *in, voi
 
 /* sar_fft_lines without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that must not have device memory
- * allocated on their behalf -- work recorded inside a CUDA stream capture,
- * real-time / on-board processors that fix their device-memory footprint at
- * start-up, applications whose device memory belongs to a pool allocator.
+ * allocated on their behalf -- real-time / on-board processors that fix
+ * their device-memory footprint at start-up, applications whose device
+ * memory belongs to a pool allocator.
  * Same arguments and results as sar_fft_lines; it calls no cudaMalloc,
  * cudaFree or allocating library routine.  Its twiddle table lives in one
  * fixed device array of 32768 complex64 values (256 KiB, held by every GPU
@@ -315,8 +315,8 @@ SAR_API sar_status sar_fft_lines(int64_t n, int64_t n_lines, const void *in, voi
  * no ordering between them) race on it, so order them.  The first call on a
  * device looks up the array's address once, and the first call at each line
  * length loads that length's kernels (CUDA loads modules lazily by default)
- * and sets their attributes once: make one call per line length on each
- * device before any stream capture. */
+ * and sets their attributes once, so it does more host work than later
+ * calls. */
 SAR_API sar_status sar_fft_lines_static(int64_t n, int64_t n_lines, const void *in, void *out, int inverse,
                                         sar_stream stream);
 

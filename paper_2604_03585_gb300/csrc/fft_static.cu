@@ -4,12 +4,11 @@
 // sar_fft_lines keeps its twiddle tables in device memory that the library
 // allocates with cudaMalloc the first time each line length is used on a
 // device.  Some callers cannot let a library allocate device memory behind
-// their back: code that records its work inside a CUDA stream capture (an
-// allocation there either fails or breaks the capture), real-time or
-// on-board radar processors that fix their whole device-memory footprint at
-// start-up and forbid any later allocation, and applications whose device
-// memory belongs to a pool allocator that a hidden cudaMalloc could fail
-// against or fragment.  This entry point serves them: its twiddle table lives
+// their back: real-time or on-board radar processors that fix their whole
+// device-memory footprint at start-up and forbid any later allocation, and
+// applications whose device memory belongs to a pool allocator that a hidden
+// cudaMalloc could fail against or fragment.  This entry point serves them:
+// its twiddle table lives
 // in a fixed file-scope device array that exists once the CUDA module holding
 // it is loaded (with CUDA's lazy module loading, the default, that happens on
 // first use, not when the library is opened), and it calls no cudaMalloc,
@@ -30,8 +29,8 @@
 //   * the first call on each device looks up the array's device address once
 //     (cudaGetSymbolAddress) with that device current; the first call at each
 //     line length on a device loads that length's kernels (lazy loading) and
-//     sets their shared-memory limits, once.  Make one call per line length
-//     on each device before any stream capture.
+//     sets their shared-memory limits, once, so it does more host work than
+//     the calls after it.
 #include <mutex>
 
 #include "../../include/sar.h"

@@ -1,9 +1,8 @@
 """The allocation-free line FFT (sar_fft_lines_static) against sar_fft_lines.
 
 sar_fft_lines_static is for callers that must not have device memory
-allocated on their behalf -- work recorded inside a CUDA stream capture,
-on-board or real-time radar processing with a device-memory footprint fixed at
-start-up, memory owned by a pool allocator.  Its twiddles live in one fixed
+allocated on their behalf -- on-board or real-time radar processing with a
+device-memory footprint fixed at start-up, memory owned by a pool allocator.  Its twiddles live in one fixed
 device array that every call shares and rewrites.  This test calls it through
 the C-ABI twice in a row (two different lengths, so the second call must
 rebuild the shared table the first one left behind) and compares each result
