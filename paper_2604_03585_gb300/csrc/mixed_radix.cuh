@@ -409,6 +409,8 @@ struct MixedCtGeom {
     }
     static constexpr int NB = boxes(), BR = box_rows(NB);
     static constexpr int NIT = (2 * NQ + kMixedThreads - 1) / kMixedThreads;   // float4 staged per thread
+    static_assert(BR % 4 == 0 && BR <= 256 && NB * BR >= NQ && (NB - 1) * BR < NQ, "boxes cover the plane once");
+    static_assert(NB * BR * 4 <= CAP && 4 * RS <= CAP, "staged boxes and receive rows fit the shared memory");
 };
 
 template <int N, int RA, int RB, int RC, int T, int MINB, int PADDIV, bool TMA>
