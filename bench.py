@@ -567,6 +567,38 @@ def any_length_bench(sar, dev, stream, peak, reps: int = 20) -> dict:
         times.sort()
         out[str(n)]["fft_gb_s"] = 16.0 * n * n_lines / (times[len(times) // 2] * 1e-3) / 1e9
         del data
+    # whole scenes at 7-smooth range lengths: the range pass with the corner
+    # turn folded in (mixed radix) and the azimuth pass, against the three
+    # separate kernels; two rotating raw buffers, ms per scene over 20 scenes
+    scenes = {}
+    for n_range, n_az in ((3000, 3000), (5000, 5000), (1000, 16384)):
+        Hr = torch.ones(n_range, dtype=torch.complex64, device=dev)
+        Ha = torch.ones(n_az, dtype=torch.complex64, device=dev)
+        raws = [torch.randn(n_az, n_range, dtype=torch.complex64, device=dev) for _ in range(2)]
+        work = torch.empty(n_az, n_range, dtype=torch.complex64, device=dev)
+        img = torch.empty(n_range, n_az, dtype=torch.complex64, device=dev)
+        torch.cuda.synchronize()
+        row = {}
+        for key, flags in (("folded", 0), ("unfolded", sar.SAR_PLAN_UNFOLDED_CORNER_TURN)):
+            plan = sar.sar_plan_create(n_range, n_az, Hr, Ha, flags=flags)
+            for i in range(3):
+                sar.sar_rda_process_oop(plan, raws[i % 2], work, img, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i in range(20):
+                sar.sar_rda_process_oop(plan, raws[i % 2], work, img, stream)
+            e1.record(stream)
+            e1.synchronize()
+            row[key + "_ms"] = e0.elapsed_time(e1) / 20
+            row[key + "_plan_folds"] = bool(sar.sar_plan_folds_corner_turn(plan))
+            plan.destroy()
+        gbs = 32.0 * n_range * n_az / (row["folded_ms"] * 1e-3) / 1e9
+        row.update({"folded_gb_s_32B": gbs, "folded_frac_hbm_32B": gbs / peak})
+        scenes[f"{n_range}x{n_az}"] = row
+        del raws, work, img
+    out["scenes"] = scenes
+    out["scenes_note"] = ("range x azimuth; GB/s over 32 B per sample (the folded range pass and the azimuth pass); "
+                          "unfolded: range pass, corner turn, azimuth pass")
     return out
 
 
